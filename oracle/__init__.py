@@ -1,0 +1,270 @@
+"""Python access to the CPU oracle (``oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg, never by the product package. The oracle is plain C built
+with gcc (``-ffp-contract=off -frounding-math``) and shares nothing with the CUDA library
+except the seeded inputs from ``synth``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-frounding-math",
+          "-fno-fast-math", "-Wall", "-Wno-unknown-pragmas"]
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` (with OpenMP when the compiler has it)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    base = ["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Result(C.Structure):
+    _fields_ = [
+        ("n_pairs", C.c_uint64),
+        ("pairs", C.POINTER(C.c_uint32)),
+        ("count", C.POINTER(C.c_uint32)),
+        ("visits", C.POINTER(C.c_uint64)),
+        ("total_visits", C.c_uint64),
+        ("n_marginal", C.c_uint64),
+        ("seconds", C.c_double),
+        ("threads", C.c_int),
+    ]
+
+
+class _Tree(C.Structure):
+    _fields_ = [
+        ("n", C.c_uint32),
+        ("height", C.c_uint32),
+        ("perm", C.POINTER(C.c_uint32)),
+        ("key", C.POINTER(C.c_uint64)),
+        ("pos", C.POINTER(C.c_float)),
+        ("inten", C.POINTER(C.c_float)),
+        ("first", C.POINTER(C.c_uint32)),
+        ("last", C.POINTER(C.c_uint32)),
+        ("split", C.POINTER(C.c_uint32)),
+        ("lo", C.POINTER(C.c_float)),
+        ("hi", C.POINTER(C.c_float)),
+        ("imax", C.POINTER(C.c_float)),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            u32, u64, f32, i32 = C.c_uint32, C.c_uint64, C.c_float, C.c_int
+            P = C.c_void_p
+            L.or_brev.restype = u32
+            L.or_brev.argtypes = [u32, i32]
+            for nm in ("or_rangemin_scan", "or_rangemin_trie"):
+                getattr(L, nm).restype = u32
+                getattr(L, nm).argtypes = [u64, u64, u32, i32, C.POINTER(u64)]
+            L.or_alg1.restype = u64
+            L.or_alg1.argtypes = [u64, u64, i32]
+            for nm in ("or_alg2_printed", "or_alg2_fixed"):
+                getattr(L, nm).restype = u64
+                getattr(L, nm).argtypes = [u64, u64, u32, i32]
+            L.or_rangemin_batch.restype = None
+            L.or_rangemin_batch.argtypes = [P, P, P, u64, i32, i32, P, P, i32]
+            L.or_fround.restype = f32
+            L.or_fround.argtypes = [i32, f32, f32, i32]
+            L.or_leaf_threshold.restype = u64
+            L.or_leaf_threshold.argtypes = [f32, P, f32, P]
+            L.or_node_threshold.restype = u64
+            L.or_node_threshold.argtypes = [f32, P, P, f32, P]
+            L.or_morton.restype = u64
+            L.or_morton.argtypes = [f32, f32, f32]
+            L.or_tree_build.restype = C.POINTER(_Tree)
+            L.or_tree_build.argtypes = [P, P, u32]
+            L.or_tree_free.restype = None
+            L.or_tree_free.argtypes = [C.POINTER(_Tree)]
+            for nm in ("or_cull_flat", "or_cull_hier"):
+                getattr(L, nm).restype = C.POINTER(_Result)
+                getattr(L, nm).argtypes = [C.POINTER(_Tree), P, P, P, P, u32, P, u32, u32, f32, i32]
+            L.or_cull_free.restype = None
+            L.or_cull_free.argtypes = [C.POINTER(_Result)]
+            L.or_max_threads.restype = i32
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---- range minimum ---------------------------------------------------------------------
+
+def brev(x: int, B: int = 32) -> int:
+    return int(lib().or_brev(x, B))
+
+
+def rangemin_scan(a: int, b: int, r: int, B: int = 32):
+    k = C.c_uint64()
+    v = lib().or_rangemin_scan(a, b, r, B, C.byref(k))
+    return int(v), int(k.value)
+
+
+def rangemin_trie(a: int, b: int, r: int, B: int = 32):
+    k = C.c_uint64()
+    v = lib().or_rangemin_trie(a, b, r, B, C.byref(k))
+    return int(v), int(k.value)
+
+
+def alg1(a: int, b: int, B: int = 32) -> int:
+    return int(lib().or_alg1(a, b, B))
+
+
+def alg2_printed(a: int, b: int, r: int, B: int = 32) -> int:
+    return int(lib().or_alg2_printed(a, b, r, B))
+
+
+def alg2_fixed(a: int, b: int, r: int, B: int = 32) -> int:
+    return int(lib().or_alg2_fixed(a, b, r, B))
+
+
+METHODS = {"scan": 0, "trie": 1, "alg2": 2, "alg2_printed": 3, "alg1": 4}
+
+
+def rangemin_batch(a, b, r, method: str = "trie", nthreads: int = 0, want_argmin: bool = True,
+                   B: int = 32):
+    a = np.ascontiguousarray(a, dtype=np.uint32)
+    b = np.ascontiguousarray(b, dtype=np.uint32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    n = len(a)
+    v = np.empty(n, dtype=np.uint32)
+    k = np.empty(n, dtype=np.uint32) if want_argmin else None
+    lib().or_rangemin_batch(_ptr(a), _ptr(b), _ptr(r), n, METHODS[method], B, _ptr(v),
+                            _ptr(k) if k is not None else None, nthreads)
+    return v, k
+
+
+# ---- thresholds --------------------------------------------------------------------------
+
+def fround(op: str, x: float, y: float, mode: int) -> np.float32:
+    ops = {"add": 0, "sub": 1, "mul": 2, "div": 3}
+    return np.float32(lib().or_fround(ops[op], np.float32(x), np.float32(y), mode))
+
+
+def leaf_threshold(tau, l, intensity, e) -> int:
+    l = np.ascontiguousarray(l, dtype=np.float32)
+    e = np.ascontiguousarray(e, dtype=np.float32)
+    return int(lib().or_leaf_threshold(np.float32(tau), _ptr(l), np.float32(intensity), _ptr(e)))
+
+
+def node_threshold(tau, lo, hi, imax, e) -> int:
+    lo = np.ascontiguousarray(lo, dtype=np.float32)
+    hi = np.ascontiguousarray(hi, dtype=np.float32)
+    e = np.ascontiguousarray(e, dtype=np.float32)
+    return int(lib().or_node_threshold(np.float32(tau), _ptr(lo), _ptr(hi), np.float32(imax), _ptr(e)))
+
+
+def morton(x, y, z) -> int:
+    return int(lib().or_morton(np.float32(x), np.float32(y), np.float32(z)))
+
+
+# ---- hierarchy and culling -----------------------------------------------------------------
+
+class Tree:
+    """Oracle light hierarchy: Morton-sorted leaves and a top-down binary radix tree."""
+
+    def __init__(self, light_pos: np.ndarray, intensity: np.ndarray):
+        self._pos = np.ascontiguousarray(light_pos, dtype=np.float32).reshape(-1, 3)
+        self._inten = np.ascontiguousarray(intensity, dtype=np.float32)
+        self.n = len(self._inten)
+        self._t = lib().or_tree_build(_ptr(self._pos), _ptr(self._inten), self.n)
+        if not self._t:
+            raise ValueError("empty light set")
+        t = self._t.contents
+        n, ni = self.n, self.n - 1
+        self.height = int(t.height)
+        self.perm = np.ctypeslib.as_array(t.perm, shape=(n,)).copy()
+        self.key = np.ctypeslib.as_array(t.key, shape=(n,)).copy()
+        self.pos = np.ctypeslib.as_array(t.pos, shape=(n * 3,)).reshape(n, 3).copy()
+        self.inten = np.ctypeslib.as_array(t.inten, shape=(n,)).copy()
+        if ni:
+            self.first = np.ctypeslib.as_array(t.first, shape=(ni,)).copy()
+            self.last = np.ctypeslib.as_array(t.last, shape=(ni,)).copy()
+            self.split = np.ctypeslib.as_array(t.split, shape=(ni,)).copy()
+            self.lo = np.ctypeslib.as_array(t.lo, shape=(ni * 3,)).reshape(ni, 3).copy()
+            self.hi = np.ctypeslib.as_array(t.hi, shape=(ni * 3,)).reshape(ni, 3).copy()
+            self.imax = np.ctypeslib.as_array(t.imax, shape=(ni,)).copy()
+        else:
+            e32 = np.zeros(0, dtype=np.uint32)
+            self.first = self.last = self.split = e32
+            self.lo = self.hi = np.zeros((0, 3), dtype=np.float32)
+            self.imax = np.zeros(0, dtype=np.float32)
+
+    def __del__(self):
+        t = getattr(self, "_t", None)
+        if t:
+            lib().or_tree_free(t)
+            self._t = None
+
+
+def _cull(fn, tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0):
+    eye_pos = np.ascontiguousarray(eye_pos, dtype=np.float32).reshape(-1, 3)
+    px = np.ascontiguousarray(px, dtype=np.uint16)
+    py = np.ascontiguousarray(py, dtype=np.uint16)
+    tile = np.ascontiguousarray(tile, dtype=np.uint32)
+    h, w = tile.shape
+    ids = None if eye_ids is None else np.ascontiguousarray(eye_ids, dtype=np.uint32)
+    n_e = len(eye_pos)
+    res = fn(tree._t, _ptr(eye_pos), _ptr(px), _ptr(py), _ptr(ids) if ids is not None else None,
+             n_e, _ptr(tile), w, h, np.float32(tau), nthreads)
+    try:
+        r = res.contents
+        n = int(r.n_pairs)
+        out = {
+            "pairs": np.ctypeslib.as_array(r.pairs, shape=(2 * n,)).reshape(n, 2).copy() if n
+            else np.zeros((0, 2), dtype=np.uint32),
+            "count": np.ctypeslib.as_array(r.count, shape=(n_e,)).copy() if n_e
+            else np.zeros(0, dtype=np.uint32),
+            "visits": np.ctypeslib.as_array(r.visits, shape=(n_e,)).copy() if (r.visits and n_e)
+            else None,
+            "total_visits": int(r.total_visits),
+            "n_marginal": int(r.n_marginal),
+            "seconds": float(r.seconds),
+            "threads": int(r.threads),
+        }
+    finally:
+        lib().or_cull_free(res)
+    return out
+
+
+def cull_flat(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0):
+    """Every (eye, light) pair tested: the definition of the accepted set."""
+    return _cull(lib().or_cull_flat, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads)
+
+
+def cull_hier(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0):
+    """Hierarchical traversal with per-eye visit counts; must equal ``cull_flat``."""
+    return _cull(lib().or_cull_hier, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads)
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())

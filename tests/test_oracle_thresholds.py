@@ -1,0 +1,136 @@
+"""Pins for the oracle's float32 acceptance thresholds (CPU only).
+
+Directed rounding is checked against exact rational arithmetic; thresholds against
+closed-form probabilities (dyadic p gives an exact integer threshold); the node bound
+against every leaf it covers (it must never be smaller, or culling would drop accepted
+connections).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+F = np.float32
+
+
+def _ulp_up(x):
+    return np.nextafter(F(x), F(np.inf))
+
+
+@pytest.mark.parametrize("op", ["add", "sub", "mul", "div"])
+def test_directed_rounding_brackets_exact_result(op):
+    rng = np.random.default_rng({"add": 1, "sub": 2, "mul": 3, "div": 4}[op])
+    xs = (rng.standard_normal(3000) * 10.0 ** rng.integers(-8, 8, 3000)).astype(F)
+    ys = (rng.standard_normal(3000) * 10.0 ** rng.integers(-8, 8, 3000)).astype(F)
+    fn = {"add": lambda a, b: a + b, "sub": lambda a, b: a - b,
+          "mul": lambda a, b: a * b, "div": lambda a, b: a / b}[op]
+    for x, y in zip(xs, ys):
+        if op == "div" and y == 0:
+            continue
+        exact = fn(Fraction(float(x)), Fraction(float(y)))
+        lo = oracle.fround(op, x, y, -1)
+        hi = oracle.fround(op, x, y, +1)
+        rn = oracle.fround(op, x, y, 0)
+        assert Fraction(float(lo)) <= exact <= Fraction(float(hi))
+        if Fraction(float(lo)) == exact:
+            assert lo == hi
+        else:
+            assert hi == _ulp_up(lo)
+        assert rn in (lo, hi)
+
+
+def test_directed_rounding_simple_cases():
+    assert oracle.fround("add", 1.0, 2.0 ** -30, -1) == F(1.0)
+    assert oracle.fround("add", 1.0, 2.0 ** -30, +1) == _ulp_up(1.0)
+    assert oracle.fround("add", 1.0, 2.0 ** -30, 0) == F(1.0)
+    third_lo = oracle.fround("div", 1.0, 3.0, -1)
+    third_hi = oracle.fround("div", 1.0, 3.0, +1)
+    assert third_hi == _ulp_up(third_lo) and Fraction(float(third_lo)) < Fraction(1, 3)
+
+
+def _exact_threshold(p):
+    """ceil(p * 2^32) for a float32 p, exactly."""
+    p = Fraction(float(p))
+    if p <= 0:
+        return 0
+    if p >= 1:
+        return 1 << 32
+    n = p * (1 << 32)
+    return -((-n.numerator) // n.denominator)
+
+
+def test_leaf_threshold_closed_forms():
+    e = np.zeros(3, F)
+    one = F(1.0)
+    md = F(1e-4)
+    # light on the eye: the distance floor 1e-4 applies; tau = p * 1e-4 gives exactly p
+    for p, t in ((0.5, 1 << 31), (0.25, 1 << 30), (0.125, 1 << 29)):
+        assert oracle.leaf_threshold(F(p) * md, e, one, e) == t
+    assert oracle.leaf_threshold(F(0.0), e, one, e) == 0
+    assert oracle.leaf_threshold(F(1e30), e, one, e) == 1 << 32
+    # unit distance along x: p = tau * I
+    l = np.array([1.0, 0.0, 0.0], F)
+    assert oracle.leaf_threshold(F(0.25), l, one, e) == 1 << 30
+    assert oracle.leaf_threshold(F(0.5), l, F(0.5), e) == 1 << 30
+    # d^2 = 0.75, tau * I = 0.375 -> p = 0.5
+    l = np.array([0.5, 0.5, 0.5], F)
+    assert oracle.leaf_threshold(F(0.375), l, one, e) == 1 << 31
+    # non-dyadic p: ceil of the exact scaled float
+    l = np.array([1.0, 0.0, 0.0], F)
+    assert oracle.leaf_threshold(F(0.1), l, one, e) == _exact_threshold(F(0.1))
+    assert oracle.leaf_threshold(F(0.3), l, one, e) == _exact_threshold(F(0.3))
+
+
+def test_leaf_threshold_monotone_in_distance_and_intensity():
+    e = np.zeros(3, F)
+    ts = [oracle.leaf_threshold(F(0.01), np.array([d, 0, 0], F), F(1), e)
+          for d in np.linspace(0.0, 2.0, 200)]
+    assert all(x >= y for x, y in zip(ts, ts[1:]))
+    ts = [oracle.leaf_threshold(F(0.01), np.array([0.3, 0.1, 0], F), F(i), e)
+          for i in np.linspace(0.0, 20.0, 200)]
+    assert all(x <= y for x, y in zip(ts, ts[1:]))
+
+
+def test_node_bound_covers_every_leaf():
+    rng = np.random.default_rng(5)
+    for _ in range(400):
+        n = int(rng.integers(1, 12))
+        pts = rng.random((n, 3)).astype(F) * F(rng.random() * 2)
+        inten = np.exp(rng.standard_normal(n) * 1.5).astype(F)
+        lo, hi = pts.min(axis=0), pts.max(axis=0)
+        e = (rng.random(3) * 3 - 1).astype(F)
+        if rng.random() < 0.2:
+            e = pts[0].copy()  # eye exactly on a light: distance floor applies
+        tau = F(10.0 ** rng.uniform(-6, 0))
+        bound = oracle.node_threshold(tau, lo, hi, inten.max(), e)
+        leaves = [oracle.leaf_threshold(tau, p, i, e) for p, i in zip(pts, inten)]
+        assert bound >= max(leaves)
+
+
+def test_node_bound_of_single_light_is_tight():
+    # a degenerate box around one light: the bound may exceed the leaf threshold only by
+    # the few ulps the directed roundings add
+    rng = np.random.default_rng(6)
+    for _ in range(500):
+        p = rng.random(3).astype(F)
+        e = rng.random(3).astype(F)
+        i = F(np.exp(rng.standard_normal()))
+        tau = F(10.0 ** rng.uniform(-5, -2))
+        leaf = oracle.leaf_threshold(tau, p, i, e)
+        node = oracle.node_threshold(tau, p, p, i, e)
+        assert leaf <= node
+        if leaf < (1 << 32):
+            assert node - leaf <= max(4, leaf * 2 ** -20)
+
+
+def test_node_bound_zero_and_saturated():
+    e = np.zeros(3, F)
+    lo = np.array([1, 1, 1], F)
+    hi = np.array([2, 2, 2], F)
+    assert oracle.node_threshold(F(0), lo, hi, F(5), e) == 0
+    assert oracle.node_threshold(F(1e30), lo, hi, F(5), e) == 1 << 32
+    # eye inside the box: distance bound 0 -> floor 1e-4
+    inside = np.array([1.5, 1.5, 1.5], F)
+    assert oracle.node_threshold(F(0.5) * F(1e-4), lo, hi, F(1), inside) >= 1 << 31
