@@ -1,0 +1,391 @@
+"""Benchmark of blue-noise dithered QMC hierarchical Russian roulette on one GB300.
+
+One step is one pass of the whole culling path over one frame: build the light hierarchy
+(Morton keys, radix sort, radix tree, refit) and cull every eye against it, on the
+frame-sized workload (1920x1080 eyes on a heightfield, 2^20 Gaussian-mixture lights,
+64x64 blue-noise shift tile, tau for ~64 accepted lights per eye). Inputs are resident in
+HBM when timing starts; L2 is flushed between steps (a 512 MiB write outside the step's
+events). The metric is effective pairs/s = N_e * N_l / step time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs its own frame (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "effective pairs/s (N_e*N_l/time) at 2M x 1M"
+UNIT = "pairs/s"
+L2_FLUSH_BYTES = 512 << 20
+# measured peaks of this GPU type (written by the benchmark driver); fallbacks otherwise
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(n_lights=1 << 20, width=1920, height=1080):
+    import synth
+    return synth.scene_frame(width=width, height=height, n_lights=n_lights)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.rows = []
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else f"GPU-{uuid}"]
+        except Exception:
+            sel = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1907_12343_gb300 as hrr
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    s = workload()
+    n_e, n_l = len(s.eye_pos), len(s.light_pos)
+    stream = torch.cuda.Stream(dev)
+    ctx = hrr.Context(local, stream)
+    ctx.set_shift_tile(s.tile)
+
+    with torch.cuda.stream(stream):
+        lp = torch.from_numpy(s.light_pos).to(dev)
+        ep = torch.from_numpy(s.eye_pos).to(dev)
+        L = [lp[:, k].contiguous() for k in range(3)] + [torch.from_numpy(s.intensity).to(dev)]
+        E = [ep[:, k].contiguous() for k in range(3)]
+        px = torch.from_numpy(s.px.view(np.int16)).to(dev)
+        py = torch.from_numpy(s.py.view(np.int16)).to(dev)
+        cap = int(n_e * 160)
+        pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream.synchronize()
+    tau = float(s.tau)
+
+    def step():
+        tree = ctx.build_light_tree(*L)
+        st, cnt = ctx.cull(*E, px, py, tree, tau, pairs)
+        tree.free()
+        if st != hrr.HRR_OK:
+            raise RuntimeError(f"cull status {st}")
+        return cnt, tree
+
+    # warm-up
+    for _ in range(args.warmup):
+        cnt, _ = step()
+    tree = ctx.build_light_tree(*L)
+    height = tree.height
+    tree.free()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    ctx.set_timing(True)
+    launches0 = ctx.launch_count()
+    clocks.start()
+    t0 = time.perf_counter()
+    visits = []
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            cnt, _ = step()
+            ev[k][1].record(stream)
+            visits.append(ctx.last_cull_stats()[0])
+            flush.fill_(k)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    kern_ms, kern_n = ctx.kernel_time()
+    ctx.set_timing(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_rank = sum(step_ms) / len(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([t_rank], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    else:
+        t_step = t_rank
+    value = ws * n_e * n_l / t_step
+
+    # cull-only throughput and the traversal kernel's roofline figures
+    cull_ms = kern_ms / max(kern_n, 1)
+    V = statistics.median(visits)
+    peaks, kind = _peaks()
+    roof = roofline(V, cnt, n_e, cull_ms, peaks, kind, clk)
+
+    # end to end through the public API with host buffers
+    e2e = run_e2e(ctx, s, dev, stream, args, cap)
+
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
+            "config": {"workload": f"frame {1920}x{1080} eyes x {n_l} Gaussian-mixture lights, "
+                                   "64x64 blue-noise tile, ~64 accepted/eye",
+                       "n_eyes": n_e, "n_lights": n_l, "tau": tau, "tree_height": height,
+                       "step": "build light tree + cull all eyes",
+                       "l2": "flushed between steps (512 MiB write outside the step events)",
+                       "parallelism": f"replicas x{ws}"},
+            "accepted_pairs": int(cnt), "accepted_per_eye": cnt / n_e, "node_visits": int(V),
+            "cull_only": {"ms": cull_ms, "value": n_e * n_l / (cull_ms / 1e3), "unit": UNIT},
+            "wall_s": wall,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        if ws == 1 and not args.no_cpu_baseline:
+            result["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
+        print(json.dumps(result), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return result
+
+
+def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk):
+    """Traversal-kernel roofline. Algorithmic bytes per launch: one 64-byte node record per
+    visited internal node (the tree stays in the 126 MB L2 and is re-read by every eye),
+    plus 16 bytes of eye input per eye and 8 bytes per accepted pair written."""
+    bytes_per_launch = 64.0 * V + 16.0 * n_e + 8.0 * accepted
+    sec = cull_ms / 1e3
+    hbm_bytes = 16.0 * n_e + 8.0 * accepted + 64.0 * (1 << 20) + 4.0 * accepted
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    return {
+        "bound": "hbm",
+        "achieved": hbm_bytes / sec / 1e9,
+        "peak": hbm_peak,
+        "unit": "GB/s",
+        "frac": hbm_bytes / sec / 1e9 / hbm_peak,
+        "traffic": None,
+        "peak_kind": kind,
+        "kernel": "cull_kernel",
+        "kernel_ms": cull_ms,
+        "node_record_bytes_gbs": bytes_per_launch / sec / 1e9,
+        "node_visits_per_s": V / sec,
+    }
+
+
+def run_e2e(ctx, s, dev, stream, args, cap):
+    """Same metric through the C ABI with host buffers: pinned host inputs copied in,
+    hierarchy built, eyes culled, accepted pairs and count copied back, every step."""
+    import numpy as np
+    import torch
+    import paper_1907_12343_gb300 as hrr
+
+    n_e, n_l = len(s.eye_pos), len(s.light_pos)
+    host_l = [torch.from_numpy(np.ascontiguousarray(s.light_pos[:, k])).pin_memory() for k in range(3)]
+    host_l.append(torch.from_numpy(s.intensity).pin_memory())
+    host_e = [torch.from_numpy(np.ascontiguousarray(s.eye_pos[:, k])).pin_memory() for k in range(3)]
+    host_e += [torch.from_numpy(s.px.view(np.int16)).pin_memory(), torch.from_numpy(s.py.view(np.int16)).pin_memory()]
+    dev_l = [torch.empty_like(h, device=dev) for h in host_l]
+    dev_e = [torch.empty_like(h, device=dev) for h in host_e]
+    pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
+    host_pairs = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
+    h2d = sum(h.numel() * h.element_size() for h in host_l + host_e)
+    steps = max(2, min(args.steps, 5))
+    times, d2h = [], []
+    with torch.cuda.stream(stream):
+        for k in range(steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for h, d in zip(host_l + host_e, dev_l + dev_e):
+                d.copy_(h, non_blocking=True)
+            tree = ctx.build_light_tree(*dev_l)
+            st, cnt = ctx.cull(*dev_e[:3], dev_e[3], dev_e[4], tree, float(s.tau), pairs)
+            tree.free()
+            if st != hrr.HRR_OK:
+                raise RuntimeError(f"cull status {st}")
+            host_pairs[:cnt].copy_(pairs[:cnt], non_blocking=True)
+            stream.synchronize()
+            dt = time.perf_counter() - t0
+            if k > 0:  # first iteration warms the pinned buffers
+                times.append(dt)
+                d2h.append(cnt * 8 + 24)
+    t = statistics.mean(times)
+    return {"value": n_e * n_l / t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(statistics.mean(d2h)), "ms_per_step": t * 1e3, "steps": steps}
+
+
+# ---------------------------------------------------------------------------------------
+# the oracle on the host cores
+# ---------------------------------------------------------------------------------------
+
+def _oracle_sample(s, n_sample):
+    import numpy as np
+    n_e = len(s.eye_pos)
+    ids = np.linspace(0, n_e - 1, num=n_sample).round().astype(np.uint32)
+    return ids
+
+
+def cpu_baseline(s, target_seconds=15.0):
+    """Oracle hierarchical culling on the host cores over an evenly spaced eye sample,
+    scaled to a full frame: N_e N_l / (t_build + t_sample * N_e / n_sample)."""
+    import oracle
+    n_e, n_l = len(s.eye_pos), len(s.light_pos)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(s.light_pos, s.intensity)
+    t_build = time.perf_counter() - t0
+    n = 512
+    while True:
+        ids = _oracle_sample(s, n)
+        res = oracle.cull_hier(tree, s.eye_pos[ids], s.px[ids], s.py[ids], s.tile, s.tau, eye_ids=ids)
+        if res["seconds"] * 2 >= target_seconds or n >= n_e:
+            break
+        n = min(n_e, int(n * max(2.0, target_seconds / max(res["seconds"], 1e-3))))
+    t_full = t_build + res["seconds"] * n_e / n
+    return {"value": n_e * n_l / t_full, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+            "sample": f"oracle tree build over all {n_l} lights ({t_build:.2f} s) + hierarchical "
+                      f"culling of {n} evenly spaced eyes ({res['seconds']:.2f} s), scaled to "
+                      f"{n_e} eyes"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step culls a bounded eye sample on the host."""
+    import numpy as np
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    import oracle
+    s = workload()
+    n_e, n_l = len(s.eye_pos), len(s.light_pos)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(s.light_pos, s.intensity)
+    t_build = time.perf_counter() - t0
+    n = args.ref_eyes
+    ids = _oracle_sample(s, n)
+    sub = (s.eye_pos[ids], s.px[ids], s.py[ids])
+    for _ in range(args.warmup):
+        oracle.cull_hier(tree, *sub, s.tile, s.tau, eye_ids=ids)
+    times = []
+    for _ in range(args.steps):
+        res = oracle.cull_hier(tree, *sub, s.tile, s.tau, eye_ids=ids)
+        times.append(res["seconds"])
+    t = statistics.mean(times)
+    value = n * n_l / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32",
+            "data": "synthetic",
+            "config": {"workload": "frame 1920x1080 eyes x 1048576 Gaussian-mixture lights, "
+                                   "64x64 blue-noise tile, ~64 accepted/eye",
+                       "n_eyes": n_e, "n_lights": n_l, "tau": float(s.tau)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+                             "sample": f"{n} evenly spaced eyes x all {n_l} lights per step "
+                                       f"(hierarchical oracle; tree built once in {t_build:.2f} s)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-eyes", type=int, default=2048)
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

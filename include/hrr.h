@@ -1,0 +1,193 @@
+/*
+ * hrr.h - C ABI of the GB300 (sm_103a) library for blue-noise dithered QMC hierarchical
+ * Russian roulette (Pantaleoni, "Blue-Noise Dithered QMC Hierarchical Russian Roulette").
+ *
+ * The problem (Sec. 1): eye vertices e_j, j in [0, N_e), and light vertices l_i sorted by
+ * a hierarchy whose nodes are leaf ranges [a_n, b_n). Each eye owns a Cranley-Patterson
+ * rotated base-2 radical-inverse sequence
+ *     xi_j(i) = (Phi_2(i) + r_j) mod 1,
+ * with its shift r_j read from a blue-noise tile at the eye's pixel. Light i is connected
+ * to eye j iff xi_j(i) < p_ij (Russian roulette). A top-down traversal culls every
+ * subtree whose range minimum v(a_n, b_n) = min_{i in [a_n,b_n)} xi_j(i) is at least a
+ * conservative bound on p over the subtree, so the accepted set equals the brute-force
+ * set over all N_e * N_l pairs while visiting a sub-linear number of nodes.
+ *
+ * Number formats (exact, no rounding anywhere in the sequence arithmetic):
+ *   - A shift r is a uint32 fixed-point number r / 2^32; Phi_2(i) = brev32(i) / 2^32
+ *     (Sec. 2, radical inverse); xi_j(i) = brev32(i) + r_j (mod 2^32) as a uint32.
+ *   - The acceptance probability of a pair is the float32 expression
+ *       p = fminf(1, (tau * I_i) / fmaxf(d2, 1e-4f)),  d2 = (dx*dx + dy*dy) + dz*dz,
+ *     dx = l.x - e.x etc., every operation rounded to nearest, in that order, without
+ *     fused multiply-add. Its fixed-point threshold is t = ceil(p * 2^32) in [0, 2^32]
+ *     (t = 0 when p <= 0) and the pair is accepted iff xi < t.
+ *   - The node bound uses the same expression with directed rounding (gap to the box
+ *     and its squares and sums rounded down, numerator and quotient rounded up), so that
+ *     it is never below the threshold of any light in the subtree.
+ *
+ * Conventions for every call:
+ *   - Functions return an hrr_status. On failure hrr_last_error(ctx) describes it.
+ *   - "device pointer" = memory on the context's GPU; the caller owns it and must keep it
+ *     valid until the call's work on the context stream has completed.
+ *   - All work is enqueued on the context stream. Calls that return a host-visible
+ *     result (a count, an info field) synchronise that stream before returning; this is
+ *     stated per call.
+ *   - A context is not thread-safe: use one per host thread.
+ *   - The library never frees caller memory and never keeps caller pointers after a
+ *     call returns.
+ */
+#ifndef HRR_H
+#define HRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hrr_status {
+    HRR_OK = 0,
+    HRR_ERR_INVALID_ARG = 1, /* bad pointer, size, value or handle */
+    HRR_ERR_OOM = 2,         /* device or pinned-host allocation failed */
+    HRR_ERR_NO_TILE = 3,     /* hrr_cull before hrr_set_shift_tile */
+    HRR_ERR_OVERFLOW = 4,    /* output capacity too small; *out_count holds the need */
+    HRR_ERR_TIMEOUT = 5,     /* a bounded device wait or queue wait ran out */
+    HRR_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+    HRR_ERR_DEVICE = 7       /* a kernel reported an internal error flag */
+} hrr_status;
+
+typedef struct hrr_ctx hrr_ctx;   /* opaque, library-owned */
+typedef struct hrr_tree hrr_tree; /* opaque, library-owned, device-resident */
+
+/* Light vertices, device pointers, structure of arrays, n_lights entries each. Positions
+ * are quantised for the spatial sort over the unit cube [0,1)^3 (values outside are
+ * clamped to the border cells: still correct, only less coherent). All values must be
+ * finite; intensities should be >= 0 (negative ones are never accepted). */
+typedef struct hrr_lights {
+    const float *x, *y, *z;
+    const float *intensity;
+} hrr_lights;
+
+/* Eye vertices, device pointers, structure of arrays, n_eyes entries each. (px, py) is
+ * the eye's pixel; its shift is tile[(py mod h) * w + (px mod w)] (Sec. 1). */
+typedef struct hrr_eyes {
+    const float *x, *y, *z;
+    const uint16_t *px, *py;
+} hrr_eyes;
+
+/* Internal node record of the light hierarchy (64 bytes, 16-byte aligned). Internal
+ * node n is a binary radix-tree node over the Morton-sorted leaves; its leaf range is
+ * [min(n, other_end), max(n, other_end)] (inclusive) and it splits after leaf `split`:
+ * child 0 covers [first, split], child 1 covers [split + 1, last]. A child whose range
+ * has one leaf is that leaf; otherwise child 0 is internal node `split` and child 1 is
+ * internal node `split + 1`. The record stores each child's bounding box and maximum
+ * intensity (for a leaf child: its position, twice, and its intensity), so a traversal
+ * tests both children from one fetch. The root is internal node 0. */
+typedef struct hrr_node {
+    float c0_lo[3];
+    float c0_imax;
+    float c0_hi[3];
+    uint32_t split;
+    float c1_lo[3];
+    float c1_imax;
+    float c1_hi[3];
+    uint32_t other_end;
+} hrr_node;
+
+/* Optional knobs of a culling call; a NULL pointer means all defaults (zeros). */
+typedef struct hrr_cull_opts {
+    /* device pointer to n_eyes uint32, or NULL: receives the number of internal nodes
+     * each eye visited (the root counts; a node is visited iff no ancestor culled it) */
+    uint32_t *eye_visits;
+    /* range-minimum variant: 0 = closed-form successor search (default), 1 = the paper's
+     * Alg. 2 with Alg. 3 (with the a = 0 fallback to Alg. 1). Results are identical. */
+    int rangemin_variant;
+    /* added (mod 2^32) to every eye's shift: the sample offset psi(n) of the adaptive
+     * sampling variant (Sec. 3), absorbed into the shift; 0 for the plain method */
+    uint32_t shift_offset;
+} hrr_cull_opts;
+
+/* ---- context --------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`. cuda_stream is a cudaStream_t on that device
+ * (for example torch.cuda.current_stream().cuda_stream) or NULL for a stream owned by the
+ * context. Allocates a few bytes of device counters and pinned host memory. */
+int hrr_create(hrr_ctx **out, int device, void *cuda_stream);
+/* Waits for the context stream, then releases the context (not trees built with it). */
+int hrr_destroy(hrr_ctx *ctx);
+/* Text of the last error on this context ("" if none). Valid until the next call. */
+const char *hrr_last_error(const hrr_ctx *ctx);
+/* Static name of a status code. */
+const char *hrr_status_string(int status);
+/* Number of kernels this context has launched so far. */
+int hrr_launch_count(const hrr_ctx *ctx, uint64_t *out);
+/* Enable (1) or disable (0) CUDA-event timing of the traversal kernel on the context
+ * stream; hrr_kernel_time returns the summed device time (ms) and launch count since it
+ * was enabled, synchronising the stream. */
+int hrr_set_timing(hrr_ctx *ctx, int enable);
+int hrr_kernel_time(hrr_ctx *ctx, double *ms, uint64_t *launches);
+
+/* ---- light hierarchy (Sec. 1: lights sorted by a hierarchy of leaf ranges) -------------- */
+
+/* Build the light hierarchy: 63-bit Morton keys (21 bits per axis, cell =
+ * floor(x * 2^21) clamped to [0, 2^21 - 1]; bit k of the x, y, z cells at key bits
+ * 3k+2, 3k+1, 3k), a stable radix sort by (key, original index), a binary radix tree over
+ * (key, sorted position), and a bottom-up refit of boxes and maximum intensities. Leaf
+ * i of the tree is the i-th light in sorted order; i is the index of the radical-inverse
+ * sequence (Sec. 1: spatially sorted lights inherit the sequence's stratification).
+ * 1 <= n_lights <= 2^31 - 1. Synchronises the context stream; returns
+ * HRR_ERR_INVALID_ARG if any position or intensity is not finite. */
+int hrr_build_light_tree(hrr_ctx *ctx, hrr_lights lights, uint32_t n_lights, hrr_tree **out);
+/* Release a hierarchy (stream-ordered on ctx). */
+int hrr_free_light_tree(hrr_ctx *ctx, hrr_tree *tree);
+/* Device pointer to the sorted-leaf -> original light id permutation (n_lights entries). */
+int hrr_tree_perm(const hrr_tree *tree, const uint32_t **dev_perm);
+/* Size facts of a hierarchy: lights, height (internal nodes on the longest root-to-leaf
+ * path; 0 for one light), device pointer to its n_lights - 1 node records (NULL for one
+ * light). Any output pointer may be NULL. */
+int hrr_tree_info(const hrr_tree *tree, uint32_t *n_lights, uint32_t *height,
+                  const hrr_node **dev_nodes);
+/* Copy the node records and the permutation to host memory (n_lights - 1 records and
+ * n_lights ids; either pointer may be NULL). Synchronises the context stream. */
+int hrr_tree_download(hrr_ctx *ctx, const hrr_tree *tree, hrr_node *host_nodes,
+                      uint32_t *host_perm);
+
+/* ---- shifts (Sec. 1: blue-noise dithered Cranley-Patterson rotations) ------------------- */
+
+/* Copy a w x h tile of uint32 shifts (row-major, host memory) into the context. The
+ * eye at pixel (px, py) uses tile[(py mod h) * w + (px mod w)]. 1 <= w, h <= 65536.
+ * Synchronises the context stream. */
+int hrr_set_shift_tile(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, uint32_t h);
+
+/* ---- culling (Sec. 1: hierarchical Russian roulette with QMC sequences) ----------------- */
+
+/* Cull all eye x light connections. Writes the accepted pairs to dev_pairs as
+ * (eye index j, original light id) uint32 pairs, 2 * cap uint32 of device memory, in no
+ * particular order; sets *out_count to the number of accepted pairs. If that number
+ * exceeds cap, returns HRR_ERR_OVERFLOW (the first cap slots hold some accepted pairs,
+ * unspecified which) and the caller may retry with a larger buffer. tau >= 0 and finite.
+ * n_eyes may be 0. Synchronises the context stream (to read the count). */
+int hrr_cull(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
+             uint32_t *dev_pairs, uint64_t cap, uint64_t *out_count);
+/* hrr_cull with options (see hrr_cull_opts). opts may be NULL. */
+int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree,
+                float tau, const hrr_cull_opts *opts, uint32_t *dev_pairs, uint64_t cap,
+                uint64_t *out_count);
+/* Statistics of the last hrr_cull/hrr_cull_ex on this context: total internal-node
+ * visits and accepted pairs (both exact, computed on the device). */
+int hrr_last_cull_stats(const hrr_ctx *ctx, uint64_t *visits, uint64_t *accepted);
+
+/* ---- range minimum (Sec. 2, Alg. 1-3) -------------------------------------------------- */
+
+/* For q in [0, n): out_min[q] = min_{i in [a[q], b[q])} (brev32(i) + r[q]) mod 2^32 and
+ * out_argmin[q] = the unique index attaining it (v(a,b) and k of Sec. 1-2 in 32-bit fixed
+ * point). Device pointers; out_argmin may be NULL. An empty range (a >= b) gives
+ * out_min = 0xFFFFFFFF and out_argmin = 0xFFFFFFFF. variant as in hrr_cull_opts.
+ * Asynchronous (no stream synchronisation). */
+int hrr_range_min(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r,
+                  uint32_t *out_min, uint32_t *out_argmin, uint64_t n, int variant);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HRR_H */

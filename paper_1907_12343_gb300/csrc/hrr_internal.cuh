@@ -1,0 +1,273 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hrr.h"
+
+// ------------------------------------------------------------------------------------
+// Host-side objects
+// ------------------------------------------------------------------------------------
+
+struct hrr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // shift tile (library-owned copy)
+    uint32_t *tile = nullptr;
+    uint32_t tile_w = 0, tile_h = 0;
+    // device counters of the last cull: [0] accepted pairs, [1] node visits, [2] flags,
+    // [3] work cursor
+    unsigned long long *counters = nullptr;
+    unsigned long long *host_counters = nullptr;  // pinned mirror
+    uint64_t last_visits = 0, last_accepted = 0;
+    uint64_t launches = 0;
+    // optional traversal-kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_start, ev_stop;  // recorded pairs, in order
+    std::vector<cudaEvent_t> ev_pool;
+    int sm_count = 0;
+    std::string err;
+};
+
+struct hrr_tree {
+    int device = 0;
+    uint32_t n = 0;
+    uint32_t height = 0;
+    hrr_node *nodes = nullptr;  // n - 1 records (one record with the single leaf if n == 1)
+    uint32_t *perm = nullptr;   // n
+};
+
+// Status helpers (hrr_abi.cu)
+int hrr_fail(hrr_ctx *ctx, int status, const std::string &msg);
+int hrr_cuda_fail(hrr_ctx *ctx, cudaError_t e, const char *what);
+
+#define HRR_CUDA(ctx, call)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return hrr_cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+// RAII device selection for an API call
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Traversal timing (hrr_abi.cu)
+void hrr_timing_begin(hrr_ctx *ctx);
+void hrr_timing_end(hrr_ctx *ctx);
+
+// Entry points implemented per translation unit
+int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &lights, uint32_t n, hrr_tree **out);
+int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &eyes, uint32_t n_eyes, const hrr_tree *tree,
+                  float tau, const hrr_cull_opts &opts, uint32_t *pairs, uint64_t cap,
+                  uint64_t *out_count);
+int hrr_range_min_impl(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r,
+                       uint32_t *out_min, uint32_t *out_argmin, uint64_t n, int variant);
+
+// Device flags reported through counters[2]
+enum : unsigned long long {
+    HRR_FLAG_STACK = 1ull,     // traversal stack would overflow (cannot happen for valid trees)
+    HRR_FLAG_NONFINITE = 2ull, // a light position or intensity is not finite
+    HRR_FLAG_TOPOLOGY = 4ull,  // a node record or parent link is out of range
+};
+
+// ------------------------------------------------------------------------------------
+// Device math
+// ------------------------------------------------------------------------------------
+
+// Range minimum of the shifted radical inverse, closed form.
+//
+// With T = (2^32 - r) mod 2^32 (the threshold 1 - r of Sec. 2), the minimum of
+// (brev(i) + r) mod 2^32 over [a,b) sits at the smallest brev(i) >= T if any (cases one
+// and two of Sec. 2's split), else at the smallest brev(i) (case three, Alg. 1). The
+// values brev(i) form a binary trie whose level-k digit is bit k of i, and a level-k
+// prefix p is present iff a + ((p - a) mod 2^k) < b. With c = brev(T) (the paper's k_r),
+// D = c - a and L = b - a, every quantity of the successor walk is an O(1) bit
+// expression:
+//   * c is in the range (case one)               iff D < L;
+//   * the right sibling of T's path at level k   exists iff bit k of c is 0 and
+//     ((D xor 2^k) mod 2^(k+1)) < L;
+//   * with h = fls(L), that holds for every zero bit k < h of c, for k = h iff bit h of D
+//     is set or (D mod 2^h) < L - 2^h, and above h only for K = h + 1 + ctz(D >> (h+1))
+//     when (D mod 2^(h+1)) < L.
+// The deepest such level k* fixes the low k*+1 bits of the answer; its members form the
+// progression i0, i0 + 2^(k*+1), ... <= b - 1, and by the identity
+// Phi_2(l + n 2^d) = 2^-d Phi_2(n) + Phi_2(l) (Sec. 4) the smallest value among them is at
+// the multiplier with the most trailing zeros: for s in [x, y], x >= 1, that is y with
+// its bits below fls((x-1) xor y) cleared (the same rule, on [a,b), gives case three).
+__device__ __forceinline__ uint32_t hrr_most_trailing_zeros(uint32_t x, uint32_t y) {
+    // the number in [x, y] with the most trailing zero bits
+    if (x == 0u) return 0u;
+    const uint32_t h = 31u - __clz((x - 1u) ^ y);
+    return y & ~((1u << h) - 1u);
+}
+
+__device__ __forceinline__ uint32_t hrr_rangemin_closed(uint32_t a, uint32_t b, uint32_t r,
+                                                        uint32_t *argmin) {
+    const uint32_t T = 0u - r;
+    const uint32_t c = __brev(T);
+    const uint32_t L = b - a;
+    const uint32_t D = c - a;
+    uint32_t k;
+    if (D < L) {
+        k = c;
+    } else {
+        const int h = 31 - __clz(L);
+        int ks = -1;
+        const uint32_t lowD = D & ((2u << h) - 1u);  // 2u << 31 wraps to 0: mask = all ones
+        if (lowD < L) {                               // only possible when h <= 30
+            const int K = h + __ffs(D >> (h + 1));    // h + 1 + ctz; D >> (h+1) != 0 here
+            if (!((c >> K) & 1u)) ks = K;
+        }
+        if (ks < 0 && !((c >> h) & 1u)) {
+            if (((D >> h) & 1u) || (D & ((1u << h) - 1u)) < L - (1u << h)) ks = h;
+        }
+        if (ks < 0) {
+            const uint32_t low = ~c & ((1u << h) - 1u);
+            if (low) ks = 31 - __clz(low);
+        }
+        if (ks >= 0) {
+            const uint32_t mask = (2u << ks) - 1u;
+            const uint32_t i0 = a + ((D ^ (1u << ks)) & mask);
+            const uint32_t s_lo = (i0 >> ks) >> 1;
+            const uint32_t s_hi = s_lo + (((b - 1u - i0) >> ks) >> 1);
+            const uint32_t s = hrr_most_trailing_zeros(s_lo, s_hi);
+            k = ((s << ks) << 1) | (i0 & mask);
+        } else {
+            k = hrr_most_trailing_zeros(a, b - 1u);
+        }
+    }
+    *argmin = k;
+    return __brev(k) + r;
+}
+
+// The paper's algorithms in 32-bit words (64-bit registers where a step may carry past
+// bit 31). fls = highest set bit, ffs = lowest set bit, both 0-based; ffs(0) = 32.
+__device__ __forceinline__ int hrr_ffs64(uint64_t x) { return x ? __ffsll((long long)x) - 1 : 32; }
+
+// Alg. 1: the index in [a,b) with the most trailing zeros (argmin of the unshifted Phi_2).
+__device__ __forceinline__ uint64_t hrr_alg1(uint64_t a, uint64_t b) {
+    if (a == 0 || a == b - 1) return a;
+    const int b_h = 63 - __clzll((long long)b);
+    const int b_l = __ffsll((long long)a) - 1;
+    uint64_t k = a, m = a;
+    for (int i = b_l; i <= b_h - 1; ++i) {
+        m &= ~(1ull << i);
+        m |= 1ull << (i + 1);
+        if (m >= a && m < b) k = m;
+    }
+    return k;
+}
+
+// Alg. 3: refine(m, i, [a,b)).
+__device__ __forceinline__ uint64_t hrr_refine(uint64_t m, int i, uint64_t a, uint64_t b) {
+    const uint64_t keep = (i >= 64) ? ~0ull : ((1ull << i) - 1ull);
+    i = hrr_ffs64(m & ~keep);
+    while (i < 31) {
+        const uint64_t k = m + (1ull << i);
+        if (k >= a && k < b) m = k;
+        i = hrr_ffs64(m & ~((2ull << i) - 1ull));
+    }
+    return m;
+}
+
+// Alg. 2 (with Alg. 3), followed by the fallback to Alg. 1 that the a = 0 ranges need.
+__device__ __forceinline__ uint32_t hrr_rangemin_alg2(uint32_t a32, uint32_t b32, uint32_t r,
+                                                      uint32_t *argmin) {
+    const uint64_t a = a32, b = b32;
+    const uint32_t T = 0u - r;
+    const uint64_t k_r = __brev(T);
+    uint64_t k = b;
+    bool done = false;
+    if (k_r >= a && k_r < b) {
+        k = k_r;
+        done = true;
+    }
+    if (!done) {
+        const int b_h = 63 - __clzll((long long)b);
+        const int k_p = hrr_ffs64(k_r);
+        uint64_t m = k_r & ((2ull << b_h) - 1ull);
+        for (int i = b_h; i >= k_p && !done; --i) {
+            if ((m >> i) & 1ull) {
+                m &= ~(1ull << i);
+            } else {
+                uint64_t m_i = m | (1ull << i);
+                if (m_i < a) m_i |= 1ull << (i + 1);
+                m_i = hrr_refine(m_i, i + 1, a, b);
+                if (m_i >= a && m_i < b) {
+                    k = m_i;
+                    done = true;
+                }
+            }
+            if ((a >> i) & 1ull) m |= 1ull << i;
+        }
+        if (!done) {
+            m = a;
+            k = b;
+            for (int i = 0; i < 32; ++i) {
+                if (k >= a && k < b && i == k_p) break;
+                if (i > 0) m &= ~(1ull << (i - 1));
+                m |= 1ull << i;
+                if (m < a) m |= 1ull << (i + 1);
+                const uint64_t m_i = hrr_refine(m, i + 1, a, b);
+                if (m_i >= a && m_i < b) k = m_i;
+            }
+        }
+        if (!(k >= a && k < b) || (r != 0u && __brev((uint32_t)k) < T)) k = hrr_alg1(a, b);
+    }
+    *argmin = (uint32_t)k;
+    return __brev((uint32_t)k) + r;
+}
+
+// ceil(p * 2^32) in [0, 2^32]; p * 2^32 is exact in float (power-of-two scaling).
+__device__ __forceinline__ unsigned long long hrr_fixed_ceil(float p) {
+    if (!(p > 0.0f)) return 0ull;
+    if (p >= 1.0f) return 1ull << 32;
+    return __float2ull_ru(__fmul_rn(p, 4294967296.0f));
+}
+
+// Exact per-pair acceptance threshold (round to nearest, canonical order, no FMA).
+__device__ __forceinline__ unsigned long long hrr_leaf_threshold(float tau, float lx, float ly,
+                                                                 float lz, float inten, float ex,
+                                                                 float ey, float ez) {
+    const float dx = __fsub_rn(lx, ex);
+    const float dy = __fsub_rn(ly, ey);
+    const float dz = __fsub_rn(lz, ez);
+    float d2 = __fmul_rn(dx, dx);
+    d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
+    d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+    const float num = __fmul_rn(tau, inten);
+    const float q = __fdiv_rn(num, fmaxf(d2, 1e-4f));
+    return hrr_fixed_ceil(fminf(1.0f, q));
+}
+
+// Conservative node bound: >= hrr_leaf_threshold of every light in [lo, hi] with
+// intensity <= imax (monotonicity of correctly rounded operations).
+__device__ __forceinline__ unsigned long long hrr_node_threshold(float tau, float lox, float loy,
+                                                                 float loz, float hix, float hiy,
+                                                                 float hiz, float imax, float ex,
+                                                                 float ey, float ez) {
+    const float gx = fmaxf(0.0f, fmaxf(__fsub_rd(lox, ex), __fsub_rd(ex, hix)));
+    const float gy = fmaxf(0.0f, fmaxf(__fsub_rd(loy, ey), __fsub_rd(ey, hiy)));
+    const float gz = fmaxf(0.0f, fmaxf(__fsub_rd(loz, ez), __fsub_rd(ez, hiz)));
+    float d2 = __fmul_rd(gx, gx);
+    d2 = __fadd_rd(d2, __fmul_rd(gy, gy));
+    d2 = __fadd_rd(d2, __fmul_rd(gz, gz));
+    const float num = __fmul_ru(tau, fmaxf(imax, 0.0f));
+    const float q = __fdiv_ru(num, fmaxf(d2, 1e-4f));
+    return hrr_fixed_ceil(fminf(1.0f, q));
+}

@@ -1,0 +1,97 @@
+"""GPU parity of the light hierarchy: Morton order, radix-tree topology, boxes and maximum
+intensities equal the oracle's top-down build, node by node (bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import upload_scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1907_12343_gb300 as hrr
+    c = hrr.Context(0)
+    yield c
+    c.close()
+
+
+def _compare(ctx, pos, inten):
+    g = upload_scene({"light_pos": pos, "intensity": inten, "eye_pos": pos[:1], "px": np.zeros(1, np.uint16),
+                      "py": np.zeros(1, np.uint16)})
+    tree = ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"])
+    nodes, perm = tree.download()
+    t = oracle.Tree(pos, inten)
+    assert np.array_equal(perm, t.perm)
+    assert tree.height == t.height
+    n = len(inten)
+    if n == 1:
+        tree.free()
+        return
+    first = np.minimum(np.arange(n - 1), nodes["other_end"])
+    last = np.maximum(np.arange(n - 1), nodes["other_end"])
+    assert np.array_equal(first, t.first) and np.array_equal(last, t.last)
+    assert np.array_equal(nodes["split"], t.split)
+    s = nodes["split"].astype(np.int64)
+    for c, cid, leaf in ((0, s, first == s), (1, s + 1, last == s + 1)):
+        lo = nodes[f"c{c}_lo"]
+        hi = nodes[f"c{c}_hi"]
+        im = nodes[f"c{c}_imax"]
+        li = cid[leaf]
+        assert np.array_equal(lo[leaf], t.pos[li]) and np.array_equal(hi[leaf], t.pos[li])
+        assert np.array_equal(im[leaf], t.inten[li])
+        ii = cid[~leaf]
+        assert np.array_equal(lo[~leaf], t.lo[ii]) and np.array_equal(hi[~leaf], t.hi[ii])
+        assert np.array_equal(im[~leaf], t.imax[ii])
+    tree.free()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 64, 1000, 4097])
+def test_uniform_lights(ctx, n):
+    rng = np.random.default_rng(n)
+    pos = rng.random((n, 3)).astype(np.float32)
+    inten = np.exp(rng.standard_normal(n)).astype(np.float32)
+    _compare(ctx, pos, inten)
+
+
+def test_duplicate_keys(ctx):
+    rng = np.random.default_rng(3)
+    pos = (rng.integers(0, 4, (20000, 3)) / 4.0).astype(np.float32)
+    _compare(ctx, pos, rng.random(20000).astype(np.float32))
+    _compare(ctx, np.full((777, 3), 0.3, np.float32), np.ones(777, np.float32))
+
+
+def test_outside_unit_cube_is_clamped(ctx):
+    rng = np.random.default_rng(4)
+    pos = (rng.random((5000, 3)) * 3 - 1).astype(np.float32)
+    _compare(ctx, pos, rng.random(5000).astype(np.float32))
+
+
+def test_gaussian_mixture_ragged(ctx):
+    pos = synth.gaussian_mixture_lights(100003, 64, seed=5)
+    inten = np.exp(1.5 * synth.normal(5, 6, 100003)).astype(np.float32)
+    _compare(ctx, pos, inten)
+
+
+def test_full_size_frame_lights(ctx):
+    s = synth.scene_frame()
+    _compare(ctx, s.light_pos, s.intensity)
+
+
+def test_nonfinite_lights_rejected(ctx):
+    import paper_1907_12343_gb300 as hrr
+    pos = np.random.default_rng(1).random((100, 3)).astype(np.float32)
+    inten = np.ones(100, np.float32)
+    for bad in ("pos", "inten"):
+        p, i = pos.copy(), inten.copy()
+        if bad == "pos":
+            p[17, 1] = np.nan
+        else:
+            i[42] = np.inf
+        g = upload_scene({"light_pos": p, "intensity": i, "eye_pos": p[:1], "px": np.zeros(1, np.uint16),
+                          "py": np.zeros(1, np.uint16)})
+        with pytest.raises(hrr.HRRError) as e:
+            ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"])
+        assert e.value.status == hrr.HRR_ERR_INVALID_ARG
