@@ -152,6 +152,31 @@ int hrr_tree_info(const hrr_tree *tree, uint32_t *n_lights, uint32_t *height,
 int hrr_tree_download(hrr_ctx *ctx, const hrr_tree *tree, hrr_node *host_nodes,
                       uint32_t *host_perm);
 
+/* Build a hierarchy without allocating any memory. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc. Examples are a renderer
+ * whose device memory is owned by its own pool, a real-time thread where an allocation
+ * may stall the device, or code that must run in a fixed memory footprint. The result is
+ * the same hierarchy as hrr_build_light_tree's: n_lights - 1 node records written to
+ * dev_nodes (one record holding the single leaf when n_lights == 1) and the
+ * sorted-leaf -> original id permutation written to dev_perm (n_lights entries), both
+ * device memory the caller owns. *out_height (may be NULL) receives the height.
+ *   - Working memory is one library-wide static device array sized for
+ *     HRR_STATIC_BUILD_MAX_LIGHTS lights (about 3.6 MiB), which every GPU that loads
+ *     the library keeps until the process exits. Larger n_lights is rejected with
+ *     HRR_ERR_INVALID_ARG.
+ *   - Runs on the calling thread's current device, on cuda_stream (NULL = the legacy
+ *     default stream), and synchronises that stream before returning.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, which may load the library's GPU code); make that first
+ *     call before any stream capture.
+ *   - All calls on a device share the array: calls whose GPU work overlaps (for
+ *     example on two streams) race and produce garbage. Serialise them.
+ *   - err (may be NULL) receives a message of at most err_len bytes on failure. */
+#define HRR_STATIC_BUILD_MAX_LIGHTS 65536u
+int hrr_build_light_tree_static(hrr_lights lights, uint32_t n_lights, hrr_node *dev_nodes,
+                                uint32_t *dev_perm, uint32_t *out_height, void *cuda_stream,
+                                char *err, size_t err_len);
+
 /* ---- shifts (Sec. 1: blue-noise dithered Cranley-Patterson rotations) ------------------- */
 
 /* Copy a w x h tile of uint32 shifts (row-major, host memory) into the context. The

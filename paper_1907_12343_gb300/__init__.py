@@ -83,7 +83,10 @@ _SIGS = {
                            C.POINTER(_u64)]),
     "hrr_last_cull_stats": (_i32, [_P, C.POINTER(_u64), C.POINTER(_u64)]),
     "hrr_range_min": (_i32, [_P, _P, _P, _P, _P, _P, _u64, _i32]),
+    "hrr_build_light_tree_static": (_i32, [hrr_lights, _u32, _P, _P, C.POINTER(_u32), _P,
+                                           C.c_char_p, C.c_size_t]),
 }
+STATIC_BUILD_MAX_LIGHTS = 65536
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.restype = _res

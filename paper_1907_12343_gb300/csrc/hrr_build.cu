@@ -353,3 +353,151 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
     *out = tree;
     return HRR_OK;
 }
+
+// ------------------------------------------------------------------------------------
+// Build without allocation
+// ------------------------------------------------------------------------------------
+//
+// hrr_build_light_tree_static runs the same kernels as hrr_build_light_tree, but takes
+// its working memory from one file-scope device array instead of allocating, and writes
+// the hierarchy into arrays the caller provides. Host code must not hand the array's name
+// to a kernel (in host code it names a host-side stand-in); its device address is looked
+// up once per device with cudaGetSymbolAddress and cached.
+
+#include <cstdio>
+#include <mutex>
+
+namespace {
+
+constexpr uint32_t kStaticMaxLights = HRR_STATIC_BUILD_MAX_LIGHTS;
+
+constexpr size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
+
+constexpr size_t static_scratch_bytes(size_t n) {
+    return 2 * pad256(sizeof(uint64_t) * n)                               // keys, ping-pong
+           + pad256(sizeof(uint32_t) * n)                                 // second value buffer
+           + pad256(sizeof(uint32_t) * 256 * ((n + kTile - 1) / kTile))   // digit histograms
+           + pad256(sizeof(float4) * n)                                   // sorted lights
+           + 2 * pad256(sizeof(uint32_t) * n)                             // parent links
+           + pad256(sizeof(uint32_t) * n)                                 // arrival counters
+           + pad256(sizeof(uint32_t) * 2 * n)                             // child heights
+           + pad256(sizeof(uint32_t))                                     // root height
+           + pad256(sizeof(unsigned long long));                          // error flags
+}
+
+// The shared working memory of every hrr_build_light_tree_static call on a device
+// (about 3.6 MiB for 65536 lights), held by each device that loads the library.
+static __device__ __align__(256) unsigned char g_static_build_scratch[static_scratch_bytes(kStaticMaxLights)];
+
+std::mutex g_static_mutex;
+void *g_static_scratch_ptr[128] = {};
+
+void set_err(char *err, size_t len, const char *msg) {
+    if (err && len) snprintf(err, len, "%s", msg);
+}
+
+}  // namespace
+
+extern "C" int hrr_build_light_tree_static(hrr_lights L, uint32_t n, hrr_node *dev_nodes,
+                                           uint32_t *dev_perm, uint32_t *out_height,
+                                           void *cuda_stream, char *err, size_t err_len) {
+    set_err(err, err_len, "");
+    if (n == 0 || n > kStaticMaxLights) {
+        char msg[160];
+        snprintf(msg, sizeof msg, "n_lights = %u is outside [1, %u], the most this call's fixed "
+                 "working memory holds; use hrr_build_light_tree for larger light sets", n, kStaticMaxLights);
+        set_err(err, err_len, msg);
+        return HRR_ERR_INVALID_ARG;
+    }
+    if (!L.x || !L.y || !L.z || !L.intensity || !dev_nodes || !dev_perm) {
+        set_err(err, err_len, "a light, node or permutation array is NULL");
+        return HRR_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 128) {
+        set_err(err, err_len, "no usable current CUDA device");
+        return HRR_ERR_CUDA;
+    }
+    char *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mutex);
+        if (!g_static_scratch_ptr[dev]) {
+            void *p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_static_build_scratch);
+            if (e != cudaSuccess || !p) {
+                set_err(err, err_len, "cudaGetSymbolAddress of the build working memory failed");
+                return HRR_ERR_CUDA;
+            }
+            g_static_scratch_ptr[dev] = p;
+        }
+        scratch = static_cast<char *>(g_static_scratch_ptr[dev]);
+    }
+    char *p = scratch;
+    uint64_t *keys0 = carve<uint64_t>(p, kStaticMaxLights), *keys1 = carve<uint64_t>(p, kStaticMaxLights);
+    uint32_t *vals1 = carve<uint32_t>(p, kStaticMaxLights);
+    uint32_t *hist = carve<uint32_t>(p, 256 * ((kStaticMaxLights + kTile - 1) / kTile));
+    float4 *spos = carve<float4>(p, kStaticMaxLights);
+    uint32_t *leaf_parent = carve<uint32_t>(p, kStaticMaxLights), *int_parent = carve<uint32_t>(p, kStaticMaxLights);
+    uint32_t *arrivals = carve<uint32_t>(p, kStaticMaxLights);
+    uint32_t *child_height = carve<uint32_t>(p, 2 * (size_t)kStaticMaxLights);
+    uint32_t *root_height = carve<uint32_t>(p, 1);
+    unsigned long long *flags = carve<unsigned long long>(p, 1);
+
+    // Every call reuses the array: clear what the kernels expect to start cleared.
+    e = cudaMemsetAsync(flags, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(root_height, 0, sizeof(uint32_t), st);
+    if (n == 1) {
+        if (e == cudaSuccess) {
+            single_leaf_kernel<<<1, 1, 0, st>>>(L.x, L.y, L.z, L.intensity, dev_nodes, dev_perm, flags);
+            e = cudaGetLastError();
+        }
+    } else {
+        const uint32_t nblocks = (n + kTile - 1) / kTile;
+        const uint64_t hist_n = 256ull * nblocks;
+        if (e == cudaSuccess) e = cudaMemsetAsync(arrivals, 0, sizeof(uint32_t) * (size_t)n, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(leaf_parent, 0xFF, sizeof(uint32_t) * (size_t)n, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(int_parent, 0xFF, sizeof(uint32_t) * (size_t)n, st);
+        if (e == cudaSuccess) {
+            const unsigned g = (n + kThreads - 1) / kThreads;
+            morton_kernel<<<g, kThreads, 0, st>>>(L.x, L.y, L.z, L.intensity, n, keys0, dev_perm, flags);
+            uint64_t *kin = keys0, *kout = keys1;
+            uint32_t *vin = dev_perm, *vout = vals1;
+            for (int shift = 0; shift < 64; shift += 8) {
+                radix_hist_kernel<<<nblocks, kThreads, 0, st>>>(kin, n, shift, hist, nblocks);
+                exclusive_scan_kernel<<<1, 1024, 0, st>>>(hist, hist_n);
+                radix_scatter_kernel<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n, shift, hist, nblocks);
+                uint64_t *tk = kin; kin = kout; kout = tk;
+                uint32_t *tv = vin; vin = vout; vout = tv;
+            }
+            gather_kernel<<<g, kThreads, 0, st>>>(L.x, L.y, L.z, L.intensity, dev_perm, n, spos);
+            const unsigned gi = (n - 1 + kThreads - 1) / kThreads;
+            topology_kernel<<<gi, kThreads, 0, st>>>(keys0, n, dev_nodes, leaf_parent, int_parent);
+            refit_kernel<<<g, kThreads, 0, st>>>(spos, n, dev_nodes, leaf_parent, int_parent, arrivals,
+                                                 child_height, root_height, flags);
+            e = cudaGetLastError();
+        }
+    }
+    uint32_t height = 0;
+    unsigned long long host_flags = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&height, root_height, sizeof height, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host_flags, flags, sizeof host_flags, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        char msg[200];
+        snprintf(msg, sizeof msg, "CUDA error in the build: %s", cudaGetErrorString(e));
+        set_err(err, err_len, msg);
+        return HRR_ERR_CUDA;
+    }
+    if (host_flags & HRR_FLAG_NONFINITE) {
+        set_err(err, err_len, "a light position or intensity is not finite");
+        return HRR_ERR_INVALID_ARG;
+    }
+    if (host_flags & HRR_FLAG_TOPOLOGY) {
+        set_err(err, err_len, "inconsistent radix-tree links");
+        return HRR_ERR_DEVICE;
+    }
+    if (out_height) *out_height = height;
+    return HRR_OK;
+}
