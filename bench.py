@@ -47,8 +47,13 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload(n_lights=1 << 20, width=1920, height=1080):
+def workload(args=None):
+    """The frame workload; --eyes WxH / --lights N shrink it for profiler captures."""
     import synth
+    width, height, n_lights = 1920, 1080, 1 << 20
+    if args is not None:
+        width, height = (int(v) for v in args.eyes.lower().split("x"))
+        n_lights = args.lights
     return synth.scene_frame(width=width, height=height, n_lights=n_lights)
 
 
@@ -127,7 +132,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    s = workload()
+    s = workload(args)
     n_e, n_l = len(s.eye_pos), len(s.light_pos)
     stream = torch.cuda.Stream(dev)
     ctx = hrr.Context(local, stream)
@@ -204,7 +209,7 @@ def run_ours(args):
     roof = roofline(V, cnt, n_e, cull_ms, peaks, kind, clk)
 
     # end to end through the public API with host buffers
-    e2e = run_e2e(ctx, s, dev, stream, args, cap)
+    e2e = None if args.no_e2e else run_e2e(ctx, s, dev, stream, args, cap)
 
     result = None
     if rank == 0:
@@ -212,7 +217,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
-            "config": {"workload": f"frame {1920}x{1080} eyes x {n_l} Gaussian-mixture lights, "
+            "config": {"workload": f"frame {args.eyes} eyes x {n_l} Gaussian-mixture lights, "
                                    "64x64 blue-noise tile, ~64 accepted/eye",
                        "n_eyes": n_e, "n_lights": n_l, "tau": tau, "tree_height": height,
                        "step": "build light tree + cull all eyes",
@@ -339,7 +344,7 @@ def run_reference(args):
     if rank != 0:
         return None
     import oracle
-    s = workload()
+    s = workload(args)
     n_e, n_l = len(s.eye_pos), len(s.light_pos)
     t0 = time.perf_counter()
     tree = oracle.Tree(s.light_pos, s.intensity)
@@ -359,7 +364,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32",
             "data": "synthetic",
-            "config": {"workload": "frame 1920x1080 eyes x 1048576 Gaussian-mixture lights, "
+            "config": {"workload": f"frame {args.eyes} eyes x {n_l} Gaussian-mixture lights, "
                                    "64x64 blue-noise tile, ~64 accepted/eye",
                        "n_eyes": n_e, "n_lights": n_l, "tau": float(s.tau)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
@@ -379,6 +384,9 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-eyes", type=int, default=2048)
+    ap.add_argument("--eyes", default="1920x1080", help="frame size WxH (one eye per pixel)")
+    ap.add_argument("--lights", type=int, default=1 << 20)
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -95,8 +95,8 @@ def lib():
             L.or_fround.argtypes = [i32, f32, f32, i32]
             L.or_leaf_threshold.restype = u64
             L.or_leaf_threshold.argtypes = [f32, P, f32, P]
-            L.or_node_threshold.restype = u64
-            L.or_node_threshold.argtypes = [f32, P, P, f32, P]
+            L.or_node_culls.restype = i32
+            L.or_node_culls.argtypes = [f32, P, P, f32, P, u32]
             L.or_morton.restype = u64
             L.or_morton.argtypes = [f32, f32, f32]
             L.or_tree_build.restype = C.POINTER(_Tree)
@@ -176,11 +176,26 @@ def leaf_threshold(tau, l, intensity, e) -> int:
     return int(lib().or_leaf_threshold(np.float32(tau), _ptr(l), np.float32(intensity), _ptr(e)))
 
 
-def node_threshold(tau, lo, hi, imax, e) -> int:
+def node_culls(tau, lo, hi, imax, e, v) -> bool:
     lo = np.ascontiguousarray(lo, dtype=np.float32)
     hi = np.ascontiguousarray(hi, dtype=np.float32)
     e = np.ascontiguousarray(e, dtype=np.float32)
-    return int(lib().or_node_threshold(np.float32(tau), _ptr(lo), _ptr(hi), np.float32(imax), _ptr(e)))
+    return bool(lib().or_node_culls(np.float32(tau), _ptr(lo), _ptr(hi), np.float32(imax), _ptr(e), int(v)))
+
+
+def node_cull_floor(tau, lo, hi, imax, e) -> int:
+    """Smallest v in [0, 2^32] for which the node culls (2^32: never), by bisection (the
+    test is monotone in v)."""
+    if not node_culls(tau, lo, hi, imax, e, 0xFFFFFFFF):
+        return 1 << 32
+    lo_v, hi_v = 0, 0xFFFFFFFF  # culls(hi_v) holds, culls(lo_v) does not (v = 0 never culls)
+    while hi_v - lo_v > 1:
+        mid = (lo_v + hi_v) // 2
+        if node_culls(tau, lo, hi, imax, e, mid):
+            hi_v = mid
+        else:
+            lo_v = mid
+    return hi_v
 
 
 def morton(x, y, z) -> int:

@@ -14,7 +14,8 @@
  *   trie ................ equals scan exhaustively for small B; three-case value ranges.
  *   Alg. 1 .............. equals the scan argmin at r = 0 exhaustively for small B.
  *   Alg. 2 / Alg. 3 ..... worked examples of Sec. 2; equals scan for every a > 0.
- *   thresholds .......... directed-rounding pins; node bound >= every leaf threshold.
+ *   thresholds .......... directed-rounding pins; a node culls only ranges whose minimum
+ *                         is >= every leaf threshold inside, and culls tightly.
  *   tree ................ partition / containment invariants; brute-force radix split.
  *   culling ............. hierarchical set == flat brute-force set (Sec. 1: the
  *                         hierarchy only removes work, never changes the result).
@@ -350,14 +351,31 @@ uint64_t or_leaf_threshold(float tau, const float l[3], float intensity, const f
     return fixed_point_ceil(fminf(1.0f, q));
 }
 
-/* Conservative bound for a node with box [lo,hi] and maximum intensity imax: the same
- * expression with the distance lower-bounded and rounded down, the numerator and the
- * quotient rounded up, so that the result is >= or_leaf_threshold of every light inside
- * (monotonicity of correctly rounded operations). Per axis the gap is
- * max(0, RD(lo - e), RD(e - hi)). */
-uint64_t or_node_threshold(float tau, const float lo[3], const float hi[3], float imax,
-                           const float e[3])
+/* u32 -> float rounded toward -inf, by truncating the bits below the 24 significant
+ * ones (truncation is rounding down for a non-negative integer). */
+static float u32_to_float_rd(uint32_t v)
 {
+    int h = fls64(v);
+    if (h > 23)
+        v = (v >> (h - 23)) << (h - 23);
+    return (float)v; /* exact: at most 24 significant bits */
+}
+
+/* Can a node with box [lo,hi] and maximum intensity imax be culled when the minimum of the
+ * eye's shifted sequence over its range is v? It can when v is at least the threshold of
+ * every light inside. Per axis the gap to the box is max(0, RD(lo - e), RD(e - hi)),
+ * squared and summed rounded down, floored at 1e-4: den_D <= the float32 max(d^2, 1e-4)
+ * of any light in the box; num_U = RU(tau * max(imax, 0)) >= RN(tau * I) of any of them.
+ * Each light's quotient is then at most num_U / den_D and its rounded value at most that
+ * times (1 + 2^-24) (or below 2^-126, which needs only v >= 1). So the node is culled iff
+ *     v >= 1  and  RD(RD(v) 2^-32 * den_D) >= RU(num_U (1 + 2^-23)) < +inf,
+ * a division-free test: the left side is a lower bound of (v / 2^32) den_D and the right an
+ * upper bound of num_U (1 + 2^-24). */
+int or_node_culls(float tau, const float lo[3], const float hi[3], float imax, const float e[3],
+                  uint32_t v)
+{
+    if (v == 0)
+        return 0;
     float d2 = 0.0f;
     for (int k = 0; k < 3; ++k) {
         float below = sub_rd(lo[k], e[k]);
@@ -366,9 +384,14 @@ uint64_t or_node_threshold(float tau, const float lo[3], const float hi[3], floa
         float g2 = mul_rd(gap, gap);
         d2 = (k == 0) ? g2 : add_rd(d2, g2);
     }
+    float den = fmaxf(d2, kMinDist2);
     float num = mul_ru(tau, fmaxf(imax, 0.0f));
-    float q = div_ru(num, fmaxf(d2, kMinDist2));
-    return fixed_point_ceil(fminf(1.0f, q));
+    float rhs = mul_ru(num, 1.00000012f); /* 1 + 2^-23 */
+    if (!(rhs < INFINITY))
+        return 0;
+    float w = u32_to_float_rd(v) * 2.3283064365386963e-10f; /* * 2^-32, exact */
+    float lhs = mul_rd(w, den);
+    return lhs >= rhs;
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -631,8 +654,8 @@ or_cull_result *or_cull_flat(const or_tree *t, const float *eye_pos, const uint1
 /* Hierarchical Russian roulette (Sec. 1): top-down traversal from the root; at each
  * visited internal node both children are tested. A leaf child is accepted by the exact
  * pair test; an internal child with range [a,b) is pushed unless the minimum of the
- * shifted sequence over [a,b) is >= its conservative bound, in which case no light below
- * it can be accepted. The root is always visited. */
+ * shifted sequence over [a,b) passes the conservative cull test (or_node_culls), in which
+ * case no light below it can be accepted. The root is always visited. */
 or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint16_t *px,
                              const uint16_t *py, const uint32_t *eye_ids, uint32_t n_eyes,
                              const uint32_t *tile, uint32_t w, uint32_t h, float tau,
@@ -674,11 +697,10 @@ or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint1
                         list_push(&lists[j], i);
                 } else {
                     uint32_t k = child[c];
-                    uint64_t bound = or_node_threshold(tau, &t->lo[3 * (uint64_t)k],
-                                                       &t->hi[3 * (uint64_t)k], t->imax[k], e);
                     uint64_t arg;
                     uint32_t v = or_rangemin_trie(cf[c], (uint64_t)cl[c] + 1, r, 32, &arg);
-                    if ((uint64_t)v < bound)
+                    if (!or_node_culls(tau, &t->lo[3 * (uint64_t)k], &t->hi[3 * (uint64_t)k],
+                                       t->imax[k], e, v))
                         stack[sp++] = k;
                 }
             }

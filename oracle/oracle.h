@@ -49,9 +49,10 @@ float or_fround(int op, float x, float y, int mode);
 /* ---- acceptance thresholds (float32, canonical operation order) ---- */
 /* t_ij = ceil(p_ij * 2^32), p_ij = min(1, (tau*I) / max(d^2, 1e-4)), round to nearest. */
 uint64_t or_leaf_threshold(float tau, const float l[3], float intensity, const float e[3]);
-/* Conservative node bound T_n >= t_ij for every light in the box with intensity <= imax. */
-uint64_t or_node_threshold(float tau, const float lo[3], const float hi[3], float imax,
-                           const float e[3]);
+/* Conservative cull test: 1 only if v >= t_ij for every light in the box [lo,hi] with
+ * intensity <= imax (v: minimum of the eye's shifted sequence over the node's range). */
+int or_node_culls(float tau, const float lo[3], const float hi[3], float imax, const float e[3],
+                  uint32_t v);
 
 /* ---- light hierarchy ---- */
 uint64_t or_morton(float x, float y, float z);

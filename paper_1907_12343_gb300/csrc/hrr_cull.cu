@@ -4,22 +4,26 @@
 // at every visited internal node, tests both children from the node's 64-byte record:
 //   * a leaf child i is accepted iff brev(i) + r_j < ceil(p_ij 2^32) (exact float32 p);
 //   * an internal child with leaf range [a, b) is descended unless the range minimum
-//     v(a, b) = min_{i in [a,b)} (brev(i) + r_j) mod 2^32 is >= its conservative bound
-//     T = ceil(P 2^32), P >= p_ij for every light below it (then none can be accepted).
+//     v(a, b) = min_{i in [a,b)} (brev(i) + r_j) mod 2^32 passes the conservative cull test
+//     (v is at least the threshold of every light below; then none can be accepted).
 // The accepted set therefore equals flat Russian roulette over all pairs.
 //
-// Execution: one eye per thread; a warp steps its 32 traversals together, one node per
-// lane per iteration, so that accepted pairs can be counted with two ballots and staged
-// in a per-warp shared-memory buffer; a full buffer is appended to the output with one
-// atomic and coalesced 8-byte stores.
+// Execution: a persistent grid (a whole number of resident blocks per SM). Each lane of a
+// warp traverses one eye; the warp steps its lanes together, one node per lane per
+// iteration, so accepted pairs are counted with two ballots and staged in a per-warp
+// shared-memory buffer that is appended to the output with one atomic and coalesced
+// 8-byte stores. When lanes finish their eyes the warp refills them from a global eye
+// cursor (one atomic per refill), which keeps the warp's lanes busy until the eyes run
+// out instead of waiting for its slowest traversal.
 #include "hrr_internal.cuh"
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kBuf = 256;     // staged pairs per warp
-constexpr int kStack = 96;    // >= height of any radix tree over 95-bit ordering keys
+constexpr int kBuf = 256;         // staged pairs per warp
+constexpr int kStack = 96;        // >= height of any radix tree over 95-bit ordering keys
+constexpr int kRefillBelow = 29;  // refill once at least 4 lanes are idle
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 struct CullParams {
@@ -34,7 +38,7 @@ struct CullParams {
     float tau;
     uint2 *pairs;
     unsigned long long cap;
-    unsigned long long *counters;  // [0] accepted, [1] visits, [2] flags
+    unsigned long long *counters;  // [0] accepted, [1] visits, [2] flags, [3] eye cursor
     uint32_t *eye_visits;
 };
 
@@ -74,41 +78,65 @@ __device__ __forceinline__ void emit(const CullParams &P, uint2 *wbuf, uint32_t 
     __syncwarp();
 }
 
+__device__ __forceinline__ uint32_t eye_shift(const CullParams &P, uint32_t j) {
+    const uint32_t tx = P.px[j] % P.tile_w, ty = P.py[j] % P.tile_h;
+    return P.tile[ty * P.tile_w + tx] + P.shift_offset;
+}
+
+// Is the internal child with leaf range [a, b) (b exclusive) and box / intensity in
+// (q_lo, q_hi) kept (true) or culled (false)?
+template <int VARIANT>
+__device__ __forceinline__ bool keep_child(const float4 &q_lo, const float4 &q_hi, uint32_t a,
+                                           uint32_t b, uint32_t r, float tau, float ex, float ey,
+                                           float ez) {
+    float den, rhs;
+    hrr_node_bound(tau, q_lo.x, q_lo.y, q_lo.z, q_hi.x, q_hi.y, q_hi.z, q_lo.w, ex, ey, ez, den, rhs);
+    if (!hrr_node_may_cull(b - a, den, rhs)) return true;
+    return !hrr_node_culls(range_min<VARIANT>(a, b, r), den, rhs);
+}
+
 template <int VARIANT>
 __global__ void __launch_bounds__(kThreads) cull_kernel(const CullParams P) {
     __shared__ uint2 buf[kWarps][kBuf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     uint2 *wbuf = buf[warp];
-    const uint32_t j = blockIdx.x * kThreads + threadIdx.x;
-    bool alive = j < P.n_eyes;
-    float ex = 0.f, ey = 0.f, ez = 0.f;
-    uint32_t r = 0;
-    if (alive) {
-        ex = P.ex[j];
-        ey = P.ey[j];
-        ez = P.ez[j];
-        const uint32_t tx = P.px[j] % P.tile_w, ty = P.py[j] % P.tile_h;
-        r = P.tile[ty * P.tile_w + tx] + P.shift_offset;
-    }
     const float tau = P.tau;
-    uint32_t cnt = 0;
-    uint32_t visits = 0;
 
-    if (P.n_lights == 1) {  // the root is a leaf (record 0, slot 0)
-        uint32_t acc = kNone;
-        if (alive) {
-            const float4 q0 = P.nodes[0];
-            if ((unsigned long long)(__brev(0u) + r) < hrr_leaf_threshold(tau, q0.x, q0.y, q0.z, q0.w, ex, ey, ez))
-                acc = 0;
-        }
-        emit(P, wbuf, cnt, lane, j, acc, kNone);
-        alive = false;
-    }
-
+    bool alive = false;
+    bool more = true;  // warp-uniform: the eye cursor may still hand out eyes
+    uint32_t j = 0, r = 0, node = 0, visits = 0, cnt = 0;
+    float ex = 0.f, ey = 0.f, ez = 0.f;
+    unsigned long long visit_total = 0;
     uint32_t stack[kStack];
     int sp = 0;
-    uint32_t node = 0;
-    while (__any_sync(0xFFFFFFFFu, alive)) {
+
+    for (;;) {
+        unsigned alive_mask = __ballot_sync(0xFFFFFFFFu, alive);
+        if (more && __popc(alive_mask) < kRefillBelow) {
+            const unsigned idle = ~alive_mask;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&P.counters[3], (unsigned long long)__popc(idle));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (base + __popc(idle) >= P.n_eyes) more = false;
+            if (!alive) {
+                const unsigned long long jj = base + __popc(idle & lt);
+                if (jj < P.n_eyes) {
+                    j = (uint32_t)jj;
+                    ex = P.ex[j];
+                    ey = P.ey[j];
+                    ez = P.ez[j];
+                    r = eye_shift(P, j);
+                    node = 0;
+                    sp = 0;
+                    visits = 0;
+                    alive = true;
+                }
+            }
+            alive_mask = __ballot_sync(0xFFFFFFFFu, alive);
+        }
+        if (alive_mask == 0u) break;
+
         uint32_t acc0 = kNone, acc1 = kNone;
         if (alive) {
             ++visits;
@@ -119,53 +147,81 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(const CullParams P) {
             const uint32_t split = __float_as_uint(q1.w);
             const uint32_t other = __float_as_uint(q3.w);
             const uint32_t first = min(node, other), last = max(node, other);
+            bool go0 = false, go1 = false;
             if (last >= P.n_lights || split < first || split >= last) {  // corrupt record
                 atomicOr(&P.counters[2], HRR_FLAG_TOPOLOGY);
-                alive = false;
+                sp = 0;
             } else {
-                bool go0 = false, go1 = false;
                 if (first == split) {
-                    if ((unsigned long long)(__brev(split) + r) <
-                        hrr_leaf_threshold(tau, q0.x, q0.y, q0.z, q0.w, ex, ey, ez))
+                    if (hrr_leaf_accepts(__brev(split) + r, tau, q0.x, q0.y, q0.z, q0.w, ex, ey, ez))
                         acc0 = split;
                 } else {
-                    const unsigned long long T =
-                        hrr_node_threshold(tau, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q0.w, ex, ey, ez);
-                    go0 = T > 0xFFFFFFFFull || range_min<VARIANT>(first, split + 1u, r) < T;
+                    go0 = keep_child<VARIANT>(q0, q1, first, split + 1u, r, tau, ex, ey, ez);
                 }
                 if (split + 1u == last) {
-                    if ((unsigned long long)(__brev(last) + r) <
-                        hrr_leaf_threshold(tau, q2.x, q2.y, q2.z, q2.w, ex, ey, ez))
+                    if (hrr_leaf_accepts(__brev(last) + r, tau, q2.x, q2.y, q2.z, q2.w, ex, ey, ez))
                         acc1 = last;
                 } else {
-                    const unsigned long long T =
-                        hrr_node_threshold(tau, q2.x, q2.y, q2.z, q3.x, q3.y, q3.z, q2.w, ex, ey, ez);
-                    go1 = T > 0xFFFFFFFFull || range_min<VARIANT>(split + 1u, last + 1u, r) < T;
+                    go1 = keep_child<VARIANT>(q2, q3, split + 1u, last + 1u, r, tau, ex, ey, ez);
                 }
-                if (go0 && go1) {
-                    if (sp < kStack) {
-                        stack[sp++] = split + 1u;
-                    } else {
-                        atomicOr(&P.counters[2], HRR_FLAG_STACK);
-                    }
-                    node = split;
-                } else if (go0) {
-                    node = split;
-                } else if (go1) {
-                    node = split + 1u;
-                } else if (sp > 0) {
-                    node = stack[--sp];
+            }
+            if (go0 && go1) {
+                if (sp < kStack) {
+                    stack[sp++] = split + 1u;
                 } else {
-                    alive = false;
+                    atomicOr(&P.counters[2], HRR_FLAG_STACK);
                 }
+                node = split;
+            } else if (go0) {
+                node = split;
+            } else if (go1) {
+                node = split + 1u;
+            } else if (sp > 0) {
+                node = stack[--sp];
+            } else {
+                alive = false;
+                visit_total += visits;
+                if (P.eye_visits) P.eye_visits[j] = visits;
             }
         }
         emit(P, wbuf, cnt, lane, j, acc0, acc1);
     }
     if (cnt) flush(P, wbuf, cnt, lane);
-    if (P.eye_visits && j < P.n_eyes) P.eye_visits[j] = visits;
-    const unsigned wsum = __reduce_add_sync(0xFFFFFFFFu, visits);
-    if (lane == 0 && wsum) atomicAdd(&P.counters[1], (unsigned long long)wsum);
+    // visit_total < 2^32 per lane in practice; sum both halves to stay exact regardless
+    const unsigned long long wsum =
+        (unsigned long long)__reduce_add_sync(0xFFFFFFFFu, (unsigned)(visit_total & 0xFFFFFFFFull)) +
+        ((unsigned long long)__reduce_add_sync(0xFFFFFFFFu, (unsigned)(visit_total >> 32)) << 32);
+    if (lane == 0 && wsum) atomicAdd(&P.counters[1], wsum);
+}
+
+// A one-light hierarchy: the root is a leaf (record 0, slot 0).
+__global__ void __launch_bounds__(kThreads) cull_single_light_kernel(const CullParams P) {
+    __shared__ uint2 buf[kWarps][kBuf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t j = blockIdx.x * kThreads + threadIdx.x;
+    uint32_t acc = kNone, cnt = 0;
+    if (j < P.n_eyes) {
+        const float4 q0 = P.nodes[0];
+        if (hrr_leaf_accepts(__brev(0u) + eye_shift(P, j), P.tau, q0.x, q0.y, q0.z, q0.w, P.ex[j],
+                             P.ey[j], P.ez[j]))
+            acc = 0;
+        if (P.eye_visits) P.eye_visits[j] = 0;
+    }
+    emit(P, buf[warp], cnt, lane, j, acc, kNone);
+    if (cnt) flush(P, buf[warp], cnt, lane);
+}
+
+// Resident blocks per SM of the traversal kernel (the same on every device of one type).
+template <int VARIANT>
+int blocks_per_sm() {
+    static int n = 0;
+    if (!n) {
+        int m = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, cull_kernel<VARIANT>, kThreads, 0) != cudaSuccess || m < 1)
+            m = 1;
+        n = m;
+    }
+    return n;
 }
 
 }  // namespace
@@ -190,12 +246,16 @@ int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tr
         P.cap = cap;
         P.counters = ctx->counters;
         P.eye_visits = opts.eye_visits;
-        const unsigned grid = (n_eyes + kThreads - 1) / kThreads;
         hrr_timing_begin(ctx);
-        if (opts.rangemin_variant == 0)
-            cull_kernel<0><<<grid, kThreads, 0, st>>>(P);
-        else
-            cull_kernel<1><<<grid, kThreads, 0, st>>>(P);
+        if (tree->n == 1) {
+            cull_single_light_kernel<<<(n_eyes + kThreads - 1) / kThreads, kThreads, 0, st>>>(P);
+        } else {
+            const int blocks_needed = (int)(((uint64_t)n_eyes + kThreads - 1) / kThreads);
+            if (opts.rangemin_variant == 0)
+                cull_kernel<0><<<min(blocks_per_sm<0>() * ctx->sm_count, blocks_needed), kThreads, 0, st>>>(P);
+            else
+                cull_kernel<1><<<min(blocks_per_sm<1>() * ctx->sm_count, blocks_needed), kThreads, 0, st>>>(P);
+        }
         hrr_timing_end(ctx);
         ++ctx->launches;
         HRR_CUDA(ctx, cudaGetLastError());

@@ -233,17 +233,12 @@ __device__ __forceinline__ uint32_t hrr_rangemin_alg2(uint32_t a32, uint32_t b32
     return __brev((uint32_t)k) + r;
 }
 
-// ceil(p * 2^32) in [0, 2^32]; p * 2^32 is exact in float (power-of-two scaling).
-__device__ __forceinline__ unsigned long long hrr_fixed_ceil(float p) {
-    if (!(p > 0.0f)) return 0ull;
-    if (p >= 1.0f) return 1ull << 32;
-    return __float2ull_ru(__fmul_rn(p, 4294967296.0f));
-}
-
-// Exact per-pair acceptance threshold (round to nearest, canonical order, no FMA).
-__device__ __forceinline__ unsigned long long hrr_leaf_threshold(float tau, float lx, float ly,
-                                                                 float lz, float inten, float ex,
-                                                                 float ey, float ez) {
+// Exact per-pair test (round to nearest, canonical order, no FMA): accept iff
+// xi < ceil(p 2^32), p = min(1, (tau I) / max(d2, 1e-4)). For 0 < p < 1, p 2^32 is an
+// exact float below 2^32, so its ceiling fits in 32 bits.
+__device__ __forceinline__ bool hrr_leaf_accepts(uint32_t xi, float tau, float lx, float ly,
+                                                 float lz, float inten, float ex, float ey,
+                                                 float ez) {
     const float dx = __fsub_rn(lx, ex);
     const float dy = __fsub_rn(ly, ey);
     const float dz = __fsub_rn(lz, ez);
@@ -251,23 +246,45 @@ __device__ __forceinline__ unsigned long long hrr_leaf_threshold(float tau, floa
     d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
     d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
     const float num = __fmul_rn(tau, inten);
-    const float q = __fdiv_rn(num, fmaxf(d2, 1e-4f));
-    return hrr_fixed_ceil(fminf(1.0f, q));
+    const float p = fminf(1.0f, __fdiv_rn(num, fmaxf(d2, 1e-4f)));
+    if (p >= 1.0f) return true;
+    if (!(p > 0.0f)) return false;
+    return xi < __float2uint_ru(__fmul_rn(p, 4294967296.0f));
 }
 
-// Conservative node bound: >= hrr_leaf_threshold of every light in [lo, hi] with
-// intensity <= imax (monotonicity of correctly rounded operations).
-__device__ __forceinline__ unsigned long long hrr_node_threshold(float tau, float lox, float loy,
-                                                                 float loz, float hix, float hiy,
-                                                                 float hiz, float imax, float ex,
-                                                                 float ey, float ez) {
+// Conservative cull test of a node with box [lo, hi] and maximum intensity imax.
+// den = max(RD gap^2 sum, 1e-4) is at most the float32 max(d2, 1e-4) of any light in the
+// box; rhs = RU(RU(tau max(imax, 0)) (1 + 2^-23)) bounds num_i (1 + 2^-24) from above for
+// every light. The node is culled at range minimum v iff v >= 1, rhs < inf and
+// RD(RD(v) 2^-32 den) >= rhs: then v / 2^32 >= RN(num_i / den_i) for every light i, so v is
+// at least every leaf threshold (monotonicity of correctly rounded operations).
+__device__ __forceinline__ void hrr_node_bound(float tau, float lox, float loy, float loz,
+                                               float hix, float hiy, float hiz, float imax,
+                                               float ex, float ey, float ez, float &den,
+                                               float &rhs) {
     const float gx = fmaxf(0.0f, fmaxf(__fsub_rd(lox, ex), __fsub_rd(ex, hix)));
     const float gy = fmaxf(0.0f, fmaxf(__fsub_rd(loy, ey), __fsub_rd(ey, hiy)));
     const float gz = fmaxf(0.0f, fmaxf(__fsub_rd(loz, ez), __fsub_rd(ez, hiz)));
     float d2 = __fmul_rd(gx, gx);
     d2 = __fadd_rd(d2, __fmul_rd(gy, gy));
     d2 = __fadd_rd(d2, __fmul_rd(gz, gz));
-    const float num = __fmul_ru(tau, fmaxf(imax, 0.0f));
-    const float q = __fdiv_ru(num, fmaxf(d2, 1e-4f));
-    return hrr_fixed_ceil(fminf(1.0f, q));
+    den = fmaxf(d2, 1e-4f);
+    rhs = __fmul_ru(__fmul_ru(tau, fmaxf(imax, 0.0f)), 1.00000012f);
+}
+
+__device__ __forceinline__ bool hrr_node_culls(uint32_t v, float den, float rhs) {
+    if (v == 0u || !(rhs < __int_as_float(0x7f800000))) return false;
+    const float w = __fmul_rn(__uint2float_rd(v), 2.3283064365386963e-10f);  // exact * 2^-32
+    return __fmul_rd(w, den) >= rhs;
+}
+
+// Could any range of length L >= 1 be culled? Its minimum is below 2^(33 - fls(L)): the
+// values brev(i) of 2^h consecutive indices fall one into each dyadic interval of width
+// 2^(32-h), so the interval after the one holding 1 - r (cyclically) holds a value less
+// than 2^(33-h) above it. If even that bound cannot cull, the range minimum is not needed.
+__device__ __forceinline__ bool hrr_node_may_cull(uint32_t L, float den, float rhs) {
+    if (!(rhs < __int_as_float(0x7f800000))) return false;
+    const int h = 31 - __clz(L);
+    const float wmax = __int_as_float((128 - h) << 23);  // 2^(1 - h)
+    return __fmul_rd(wmax, den) >= rhs;
 }

@@ -1,9 +1,9 @@
 """Pins for the oracle's float32 acceptance thresholds (CPU only).
 
 Directed rounding is checked against exact rational arithmetic; thresholds against
-closed-form probabilities (dyadic p gives an exact integer threshold); the node bound
-against every leaf it covers (it must never be smaller, or culling would drop accepted
-connections).
+closed-form probabilities (dyadic p gives an exact integer threshold); the node cull test
+against every leaf it covers (a node may cull only at range minima that reject every light
+inside, or culling would drop accepted connections) and for tightness.
 """
 from fractions import Fraction
 
@@ -93,9 +93,11 @@ def test_leaf_threshold_monotone_in_distance_and_intensity():
     assert all(x <= y for x, y in zip(ts, ts[1:]))
 
 
-def test_node_bound_covers_every_leaf():
+def test_node_culls_only_above_every_leaf():
+    # soundness: the smallest range minimum at which a node culls is >= the acceptance
+    # threshold of every light inside it, so culling never drops an accepted connection
     rng = np.random.default_rng(5)
-    for _ in range(400):
+    for _ in range(300):
         n = int(rng.integers(1, 12))
         pts = rng.random((n, 3)).astype(F) * F(rng.random() * 2)
         inten = np.exp(rng.standard_normal(n) * 1.5).astype(F)
@@ -104,33 +106,53 @@ def test_node_bound_covers_every_leaf():
         if rng.random() < 0.2:
             e = pts[0].copy()  # eye exactly on a light: distance floor applies
         tau = F(10.0 ** rng.uniform(-6, 0))
-        bound = oracle.node_threshold(tau, lo, hi, inten.max(), e)
+        floor = oracle.node_cull_floor(tau, lo, hi, inten.max(), e)
         leaves = [oracle.leaf_threshold(tau, p, i, e) for p, i in zip(pts, inten)]
-        assert bound >= max(leaves)
+        assert floor >= max(leaves)
+        if floor < (1 << 32):
+            assert oracle.node_culls(tau, lo, hi, inten.max(), e, floor)
+            assert not oracle.node_culls(tau, lo, hi, inten.max(), e, floor - 1)
 
 
-def test_node_bound_of_single_light_is_tight():
-    # a degenerate box around one light: the bound may exceed the leaf threshold only by
-    # the few ulps the directed roundings add
+def test_node_culls_is_monotone_in_the_minimum():
+    rng = np.random.default_rng(7)
+    lo = np.array([0.2, 0.2, 0.2], F)
+    hi = np.array([0.4, 0.5, 0.3], F)
+    e = np.array([0.9, 0.1, 0.5], F)
+    for _ in range(300):
+        tau = F(10.0 ** rng.uniform(-4, -1))
+        v = int(rng.integers(0, 2**32 - 1))
+        if oracle.node_culls(tau, lo, hi, F(3), e, v):
+            assert oracle.node_culls(tau, lo, hi, F(3), e, v + 1)
+            assert oracle.node_culls(tau, lo, hi, F(3), e, 0xFFFFFFFF)
+
+
+def test_node_cull_floor_of_single_light_is_tight():
+    # a degenerate box around one light: the cull floor may exceed the leaf threshold only
+    # by the few ulps the directed roundings and the (1 + 2^-23) margin add
     rng = np.random.default_rng(6)
-    for _ in range(500):
+    for _ in range(300):
         p = rng.random(3).astype(F)
         e = rng.random(3).astype(F)
         i = F(np.exp(rng.standard_normal()))
         tau = F(10.0 ** rng.uniform(-5, -2))
         leaf = oracle.leaf_threshold(tau, p, i, e)
-        node = oracle.node_threshold(tau, p, p, i, e)
-        assert leaf <= node
+        floor = oracle.node_cull_floor(tau, p, p, i, e)
+        assert leaf <= floor
         if leaf < (1 << 32):
-            assert node - leaf <= max(4, leaf * 2 ** -20)
+            assert floor - leaf <= max(4, leaf * 2 ** -20)
 
 
-def test_node_bound_zero_and_saturated():
+def test_node_culls_zero_and_saturated():
     e = np.zeros(3, F)
     lo = np.array([1, 1, 1], F)
     hi = np.array([2, 2, 2], F)
-    assert oracle.node_threshold(F(0), lo, hi, F(5), e) == 0
-    assert oracle.node_threshold(F(1e30), lo, hi, F(5), e) == 1 << 32
-    # eye inside the box: distance bound 0 -> floor 1e-4
+    # tau = 0: nothing below can be accepted; any positive minimum culls, v = 0 never does
+    assert oracle.node_cull_floor(F(0), lo, hi, F(5), e) == 1
+    assert not oracle.node_culls(F(0), lo, hi, F(5), e, 0)
+    # p saturates at 1: never culled
+    assert oracle.node_cull_floor(F(1e30), lo, hi, F(5), e) == 1 << 32
+    # eye inside the box with p = 1/2 at the distance floor: the floor is about 2^31
     inside = np.array([1.5, 1.5, 1.5], F)
-    assert oracle.node_threshold(F(0.5) * F(1e-4), lo, hi, F(1), inside) >= 1 << 31
+    f = oracle.node_cull_floor(F(0.5) * F(1e-4), lo, hi, F(1), inside)
+    assert (1 << 31) <= f <= (1 << 31) + 2**10
