@@ -240,26 +240,69 @@ def run_ours(args):
     return result
 
 
+# Algorithmic work of one node visit on the frame workload (derivation in the design doc, sec. 6):
+# 1.963 internal child tests x 27 float ops (bound + cull predicate) + 0.977 range minima x
+# 51 integer ops + 0.774 inherited minima x 2 + 0.037 leaf tests x 17.
+OPS_PER_VISIT = 1.963 * 27 + 0.977 * 51 + 0.774 * 2 + 0.037 * 17
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_kernel_frame_1920x1080.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
+                  for f in ("hrr_cull.cu", "hrr_internal.cuh")]
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per cull launch from the committed ncu summary, if it was taken on the
+    current kernel source (null otherwise)."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
+    if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk):
-    """Traversal-kernel roofline. Algorithmic bytes per launch: one 64-byte node record per
-    visited internal node (the tree stays in the 126 MB L2 and is re-read by every eye),
-    plus 16 bytes of eye input per eye and 8 bytes per accepted pair written."""
-    bytes_per_launch = 64.0 * V + 16.0 * n_e + 8.0 * accepted
+    """Roofline of the traversal kernel, which is bound by instruction issue: the node
+    records (64 B per visit) stay in L2 and DRAM traffic is essentially the output.
+    achieved = algorithmic ops per launch (node visits x OPS_PER_VISIT) / kernel time;
+    peak = SMs x 4 schedulers x 32 lanes x maximum SM clock (one lane-op per lane per
+    clock at full issue)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * 4 * 32 * mhz * 1e6
     sec = cull_ms / 1e3
-    hbm_bytes = 16.0 * n_e + 8.0 * accepted + 64.0 * (1 << 20) + 4.0 * accepted
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = V * OPS_PER_VISIT / sec
     return {
-        "bound": "hbm",
-        "achieved": hbm_bytes / sec / 1e9,
-        "peak": hbm_peak,
-        "unit": "GB/s",
-        "frac": hbm_bytes / sec / 1e9 / hbm_peak,
-        "traffic": None,
-        "peak_kind": kind,
+        "bound": "alu",
+        "achieved": achieved / 1e12,
+        "peak": peak / 1e12,
+        "unit": "Tops/s",
+        "frac": achieved / peak,
+        "traffic": profiled_traffic(),
+        "peak_kind": f"derived from {sms} SMs x 128 lanes x {mhz:.0f} MHz ({kind} sm_max_mhz)",
         "kernel": "cull_kernel",
         "kernel_ms": cull_ms,
-        "node_record_bytes_gbs": bytes_per_launch / sec / 1e9,
+        "ops_per_visit": OPS_PER_VISIT,
         "node_visits_per_s": V / sec,
+        "node_record_bytes_gbs": 64.0 * V / sec / 1e9,
     }
 
 

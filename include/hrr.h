@@ -99,8 +99,9 @@ typedef struct hrr_cull_opts {
     /* device pointer to n_eyes uint32, or NULL: receives the number of internal nodes
      * each eye visited (the root counts; a node is visited iff no ancestor culled it) */
     uint32_t *eye_visits;
-    /* range-minimum variant: 0 = closed-form successor search (default), 1 = the paper's
-     * Alg. 2 with Alg. 3 (with the a = 0 fallback to Alg. 1). Results are identical. */
+    /* range-minimum variant, all with identical results: 0 = closed-form successor search
+     * evaluated without branches (default), 1 = the paper's Alg. 2 with Alg. 3 (with the
+     * a = 0 fallback to Alg. 1), 2 = the closed form with branches */
     int rangemin_variant;
     /* added (mod 2^32) to every eye's shift: the sample offset psi(n) of the adaptive
      * sampling variant (Sec. 3), absorbed into the shift; 0 for the plain method */
@@ -207,7 +208,8 @@ int hrr_last_cull_stats(const hrr_ctx *ctx, uint64_t *visits, uint64_t *accepted
 /* For q in [0, n): out_min[q] = min_{i in [a[q], b[q])} (brev32(i) + r[q]) mod 2^32 and
  * out_argmin[q] = the unique index attaining it (v(a,b) and k of Sec. 1-2 in 32-bit fixed
  * point). Device pointers; out_argmin may be NULL. An empty range (a >= b) gives
- * out_min = 0xFFFFFFFF and out_argmin = 0xFFFFFFFF. variant as in hrr_cull_opts.
+ * out_min = 0xFFFFFFFF and out_argmin = 0xFFFFFFFF. variant (0, 1 or 2) as in
+ * hrr_cull_opts.
  * Asynchronous (no stream synchronisation). */
 int hrr_range_min(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r,
                   uint32_t *out_min, uint32_t *out_argmin, uint64_t n, int variant);

@@ -224,8 +224,8 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
     if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
     hrr_cull_opts o{};
     if (opts) o = *opts;
-    if (o.rangemin_variant < 0 || o.rangemin_variant > 1)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0 or 1");
+    if (o.rangemin_variant < 0 || o.rangemin_variant > 2)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2");
     DeviceGuard g(ctx->device);
     return hrr_cull_impl(ctx, eyes, n_eyes, tree, tau, o, dev_pairs, cap, out_count);
 }
@@ -247,7 +247,7 @@ int hrr_range_min(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint
     if (!ctx) return HRR_ERR_INVALID_ARG;
     if (n == 0) return HRR_OK;
     if (!a || !b || !r || !out_min) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "NULL array");
-    if (variant < 0 || variant > 1) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "variant must be 0 or 1");
+    if (variant < 0 || variant > 2) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
     DeviceGuard g(ctx->device);
     return hrr_range_min_impl(ctx, a, b, r, out_min, out_argmin, n, variant);
 }

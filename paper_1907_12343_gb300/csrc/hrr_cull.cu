@@ -14,16 +14,36 @@
 // shared-memory buffer that is appended to the output with one atomic and coalesced
 // 8-byte stores. When lanes finish their eyes the warp refills them from a global eye
 // cursor (one atomic per refill), which keeps the warp's lanes busy until the eyes run
-// out instead of waiting for its slowest traversal.
+// out instead of waiting for its slowest traversal. A node's range minimum is attained at
+// its argmin, which lies in exactly one child; carrying the argmin down with the node
+// means only the other child's minimum has to be computed.
 #include "hrr_internal.cuh"
 
 namespace {
 
+// Launch shape, fixed at compile time (the values measured fastest on GB300).
+#ifndef HRR_CULL_MIN_BLOCKS
+#define HRR_CULL_MIN_BLOCKS 5  // resident 256-thread blocks per SM (caps registers at 48)
+#endif
+#ifndef HRR_CULL_REFILL_BELOW
+#define HRR_CULL_REFILL_BELOW 29  // refill a warp's idle lanes once at least 4 are idle
+#endif
+#ifndef HRR_CULL_SMEM_LEVELS
+#define HRR_CULL_SMEM_LEVELS 12  // traversal-stack levels kept in shared memory per thread
+#endif
+#ifndef HRR_CULL_BUF
+#define HRR_CULL_BUF 128  // staged output pairs per warp
+#endif
+#ifndef HRR_CULL_PREFETCH
+#define HRR_CULL_PREFETCH 0  // prefetch the children's records into L1 once the split is known
+#endif
+
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kBuf = 256;         // staged pairs per warp
+constexpr int kBuf = HRR_CULL_BUF;  // staged pairs per warp
+constexpr int kSmemLevels = HRR_CULL_SMEM_LEVELS;
 constexpr int kStack = 96;        // >= height of any radix tree over 95-bit ordering keys
-constexpr int kRefillBelow = 29;  // refill once at least 4 lanes are idle
+constexpr int kRefillBelow = HRR_CULL_REFILL_BELOW;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 struct CullParams {
@@ -41,12 +61,6 @@ struct CullParams {
     unsigned long long *counters;  // [0] accepted, [1] visits, [2] flags, [3] eye cursor
     uint32_t *eye_visits;
 };
-
-template <int VARIANT>
-__device__ __forceinline__ uint32_t range_min(uint32_t a, uint32_t b, uint32_t r) {
-    uint32_t k;
-    return VARIANT == 0 ? hrr_rangemin_closed(a, b, r, &k) : hrr_rangemin_alg2(a, b, r, &k);
-}
 
 // Append the warp's staged pairs to the output.
 __device__ __forceinline__ void flush(const CullParams &P, const uint2 *wbuf, uint32_t cnt, int lane) {
@@ -67,7 +81,7 @@ __device__ __forceinline__ void emit(const CullParams &P, uint2 *wbuf, uint32_t 
     const unsigned b1 = __ballot_sync(0xFFFFFFFFu, acc1 != kNone);
     const uint32_t tot = __popc(b0) + __popc(b1);
     if (tot == 0) return;
-    if (cnt + tot > kBuf) {
+    if (cnt + tot > (uint32_t)kBuf) {
         flush(P, wbuf, cnt, lane);
         cnt = 0;
     }
@@ -83,21 +97,24 @@ __device__ __forceinline__ uint32_t eye_shift(const CullParams &P, uint32_t j) {
     return P.tile[ty * P.tile_w + tx] + P.shift_offset;
 }
 
-// Is the internal child with leaf range [a, b) (b exclusive) and box / intensity in
-// (q_lo, q_hi) kept (true) or culled (false)?
+// Argmin of the range minimum of (brev(i) + r) over [a, b); c = brev(2^32 - r).
 template <int VARIANT>
-__device__ __forceinline__ bool keep_child(const float4 &q_lo, const float4 &q_hi, uint32_t a,
-                                           uint32_t b, uint32_t r, float tau, float ex, float ey,
-                                           float ez) {
-    float den, rhs;
-    hrr_node_bound(tau, q_lo.x, q_lo.y, q_lo.z, q_hi.x, q_hi.y, q_hi.z, q_lo.w, ex, ey, ez, den, rhs);
-    if (!hrr_node_may_cull(b - a, den, rhs)) return true;
-    return !hrr_node_culls(range_min<VARIANT>(a, b, r), den, rhs);
+__device__ __forceinline__ uint32_t range_argmin(uint32_t a, uint32_t b, uint32_t r, uint32_t c) {
+    uint32_t k;
+    if (VARIANT == 0) return hrr_range_argmin_select(a, b, c);
+    if (VARIANT == 1) hrr_rangemin_alg2(a, b, r, &k);
+    else hrr_rangemin_closed(a, b, r, &k);
+    return k;
 }
 
 template <int VARIANT>
-__global__ void __launch_bounds__(kThreads) cull_kernel(const CullParams P) {
+__global__ void __launch_bounds__(kThreads, VARIANT == 0 ? HRR_CULL_MIN_BLOCKS : 5)
+cull_kernel(const CullParams P) {
     __shared__ uint2 buf[kWarps][kBuf];
+    // The traversal stack: its first kSmemLevels levels in shared memory ([level][thread],
+    // so that lanes at the same depth hit distinct banks), deeper levels in local memory.
+    // Keeping the hot levels out of L1 leaves L1 to the node records.
+    __shared__ uint2 sstack[kSmemLevels > 0 ? kSmemLevels : 1][kThreads];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     uint2 *wbuf = buf[warp];
@@ -105,10 +122,14 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(const CullParams P) {
 
     bool alive = false;
     bool more = true;  // warp-uniform: the eye cursor may still hand out eyes
-    uint32_t j = 0, r = 0, node = 0, visits = 0, cnt = 0;
+    uint32_t j = 0, r = 0, c = 0, node = 0, visits = 0, cnt = 0;
+    // Argmin of the current node's range minimum. Exactly one child holds it and has the
+    // same minimum, so each visit computes at most one new range minimum: the other
+    // internal child's. The root's is computed when the eye starts.
+    uint32_t kmin = 0;
     float ex = 0.f, ey = 0.f, ez = 0.f;
     unsigned long long visit_total = 0;
-    uint32_t stack[kStack];
+    uint2 deep[kStack - kSmemLevels];  // (node, argmin of its range minimum)
     int sp = 0;
 
     for (;;) {
@@ -127,7 +148,9 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(const CullParams P) {
                     ey = P.ey[j];
                     ez = P.ez[j];
                     r = eye_shift(P, j);
+                    c = __brev(0u - r);
                     node = 0;
+                    kmin = range_argmin<VARIANT>(0u, P.n_lights, r, c);
                     sp = 0;
                     visits = 0;
                     alive = true;
@@ -148,36 +171,59 @@ __global__ void __launch_bounds__(kThreads) cull_kernel(const CullParams P) {
             const uint32_t other = __float_as_uint(q3.w);
             const uint32_t first = min(node, other), last = max(node, other);
             bool go0 = false, go1 = false;
-            if (last >= P.n_lights || split < first || split >= last) {  // corrupt record
-                atomicOr(&P.counters[2], HRR_FLAG_TOPOLOGY);
+            uint32_t k0 = kNone, k1 = kNone;
+            if (last >= P.n_lights || split - first >= last - first) {  // needs first <= split < last
+                atomicOr(&P.counters[2], HRR_FLAG_TOPOLOGY);               // corrupt record
                 sp = 0;
             } else {
-                if (first == split) {
-                    if (hrr_leaf_accepts(__brev(split) + r, tau, q0.x, q0.y, q0.z, q0.w, ex, ey, ez))
-                        acc0 = split;
-                } else {
-                    go0 = keep_child<VARIANT>(q0, q1, first, split + 1u, r, tau, ex, ey, ez);
-                }
-                if (split + 1u == last) {
-                    if (hrr_leaf_accepts(__brev(last) + r, tau, q2.x, q2.y, q2.z, q2.w, ex, ey, ez))
+                const bool int0 = first != split, int1 = split + 1u != last;
+#if HRR_CULL_PREFETCH
+                // The next visit is most often a child (internal nodes split and split + 1,
+                // adjacent records): start their transfer into L1 while this node is tested.
+                if (int0) asm volatile("prefetch.global.L1 [%0];" ::"l"(&P.nodes[4 * (size_t)split]));
+                if (int1) asm volatile("prefetch.global.L1 [%0];" ::"l"(&P.nodes[4 * (size_t)split + 4]));
+#endif
+                const bool kin0 = kmin <= split;
+                uint32_t knew = kNone;
+                if (kin0 ? int1 : int0)
+                    knew = range_argmin<VARIANT>(kin0 ? split + 1u : first, kin0 ? last + 1u : split + 1u, r, c);
+                k0 = kin0 ? kmin : knew;
+                k1 = kin0 ? knew : kmin;
+                float den0, rhs0, den1, rhs1;
+                hrr_node_bound(tau, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q0.w, ex, ey, ez, den0, rhs0);
+                hrr_node_bound(tau, q2.x, q2.y, q2.z, q3.x, q3.y, q3.z, q2.w, ex, ey, ez, den1, rhs1);
+                go0 = int0 && !hrr_node_culls(__brev(k0) + r, den0, rhs0);
+                go1 = int1 && !hrr_node_culls(__brev(k1) + r, den1, rhs1);
+                if (!int0 || !int1) {  // leaf children: one test site, a second for two leaves
+                    const uint32_t i = !int0 ? split : last;
+                    const float4 ql = !int0 ? q0 : q2;
+                    if (hrr_leaf_accepts(__brev(i) + r, tau, ql.x, ql.y, ql.z, ql.w, ex, ey, ez)) acc0 = i;
+                    if (!int0 && !int1 &&
+                        hrr_leaf_accepts(__brev(last) + r, tau, q2.x, q2.y, q2.z, q2.w, ex, ey, ez))
                         acc1 = last;
-                } else {
-                    go1 = keep_child<VARIANT>(q2, q3, split + 1u, last + 1u, r, tau, ex, ey, ez);
                 }
             }
             if (go0 && go1) {
-                if (sp < kStack) {
-                    stack[sp++] = split + 1u;
+                if (sp < kSmemLevels) {
+                    sstack[sp++][threadIdx.x] = make_uint2(split + 1u, k1);
+                } else if (sp < kStack) {
+                    deep[sp++ - kSmemLevels] = make_uint2(split + 1u, k1);
                 } else {
                     atomicOr(&P.counters[2], HRR_FLAG_STACK);
                 }
                 node = split;
+                kmin = k0;
             } else if (go0) {
                 node = split;
+                kmin = k0;
             } else if (go1) {
                 node = split + 1u;
+                kmin = k1;
             } else if (sp > 0) {
-                node = stack[--sp];
+                --sp;
+                const uint2 e = sp < kSmemLevels ? sstack[sp][threadIdx.x] : deep[sp - kSmemLevels];
+                node = e.x;
+                kmin = e.y;
             } else {
                 alive = false;
                 visit_total += visits;
@@ -213,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) cull_single_light_kernel(const CullP
 
 // Resident blocks per SM of the traversal kernel (the same on every device of one type).
 template <int VARIANT>
-int blocks_per_sm() {
+int blocks_per_sm() {  // one cache per variant
     static int n = 0;
     if (!n) {
         int m = 0;
@@ -253,8 +299,10 @@ int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tr
             const int blocks_needed = (int)(((uint64_t)n_eyes + kThreads - 1) / kThreads);
             if (opts.rangemin_variant == 0)
                 cull_kernel<0><<<min(blocks_per_sm<0>() * ctx->sm_count, blocks_needed), kThreads, 0, st>>>(P);
-            else
+            else if (opts.rangemin_variant == 1)
                 cull_kernel<1><<<min(blocks_per_sm<1>() * ctx->sm_count, blocks_needed), kThreads, 0, st>>>(P);
+            else
+                cull_kernel<2><<<min(blocks_per_sm<2>() * ctx->sm_count, blocks_needed), kThreads, 0, st>>>(P);
         }
         hrr_timing_end(ctx);
         ++ctx->launches;

@@ -155,6 +155,41 @@ __device__ __forceinline__ uint32_t hrr_rangemin_closed(uint32_t a, uint32_t b, 
     return __brev(k) + r;
 }
 
+// The same computation without branches, for warps whose lanes take different cases. c =
+// brev(2^32 - r) is the eye's k_r, passed in because it is constant along a traversal.
+// Returns the argmin; the minimum is brev(argmin) + r.
+//   * The levels k where the trie branches above k_r's path form a bit mask: every zero
+//     bit of c below h = fls(L); bit h when it is zero in c and (D has bit h set or
+//     D mod 2^h < L mod 2^h); and bit K = h + 1 + ctz(D >> (h+1)) when it is zero in c and
+//     D mod 2^(h+1) < L. The deepest level is ks = fls(mask) (-1: case three).
+//   * With P = 2^(ks+1) (1 in case three), the answer lies in the residue class
+//     q = i0 mod P, i0 = a + ((D xor 2^ks) mod P): among q + X .. q + Y (multiples of P,
+//     X = i0 - q, Y = (b - 1 - q) rounded down to a multiple of P) the smallest Phi_2 is
+//     at the one with the most trailing zeros, Y with the bits below
+//     fls((X - P) xor Y) cleared (or q itself when X = 0).
+__device__ __forceinline__ uint32_t hrr_range_argmin_select(uint32_t a, uint32_t b, uint32_t c) {
+    const uint32_t L = b - a;
+    const uint32_t D = c - a;
+    const int h = 31 - __clz(L);
+    const uint32_t bh = 1u << h;
+    const uint32_t mh = bh - 1u;
+    const uint32_t Z = ~c;
+    uint32_t levels = Z & mh;
+    if (((D & bh) != 0u) || (D & mh) < (L & mh)) levels |= Z & bh;
+    const uint32_t hiD = (D >> h) >> 1;
+    if ((D & (mh | bh)) < L && hiD != 0u) levels |= Z & (bh << __ffs(hiD));  // bit K
+    const int ks = 31 - __clz(levels);  // -1 when no level: case three
+    const uint32_t bit = ks >= 0 ? (1u << (ks & 31)) : 0u;
+    const uint32_t pm = ks >= 0 ? ((bit << 1) - 1u) : 0u;  // P - 1 (all ones when ks = 31)
+    const uint32_t i0 = a + ((D ^ bit) & pm);
+    const uint32_t q = i0 & pm;
+    const uint32_t X = i0 & ~pm;
+    const uint32_t Y = (b - 1u - q) & ~pm;
+    const uint32_t g = 31u - __clz((X - pm - 1u) ^ Y);  // X - P; X >= P whenever X != 0
+    const uint32_t k = X == 0u ? q : (q | (Y & (0u - (1u << g))));
+    return D < L ? c : k;
+}
+
 // The paper's algorithms in 32-bit words (64-bit registers where a step may carry past
 // bit 31). fls = highest set bit, ffs = lowest set bit, both 0-based; ffs(0) = 32.
 __device__ __forceinline__ int hrr_ffs64(uint64_t x) { return x ? __ffsll((long long)x) - 1 : 32; }

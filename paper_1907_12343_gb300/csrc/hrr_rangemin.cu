@@ -15,7 +15,11 @@ __device__ __forceinline__ uint32_t one_query(uint32_t a, uint32_t b, uint32_t r
         *k = 0xFFFFFFFFu;
         return 0xFFFFFFFFu;
     }
-    return VARIANT == 0 ? hrr_rangemin_closed(a, b, r, k) : hrr_rangemin_alg2(a, b, r, k);
+    if (VARIANT == 0) {
+        *k = hrr_range_argmin_select(a, b, __brev(0u - r));
+        return __brev(*k) + r;
+    }
+    return VARIANT == 1 ? hrr_rangemin_alg2(a, b, r, k) : hrr_rangemin_closed(a, b, r, k);
 }
 
 template <int VARIANT, bool ARGMIN>
@@ -93,6 +97,7 @@ int launch(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r
 
 int hrr_range_min_impl(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r,
                        uint32_t *out_min, uint32_t *out_argmin, uint64_t n, int variant) {
-    return variant == 0 ? launch<0>(ctx, a, b, r, out_min, out_argmin, n)
-                        : launch<1>(ctx, a, b, r, out_min, out_argmin, n);
+    if (variant == 0) return launch<0>(ctx, a, b, r, out_min, out_argmin, n);
+    if (variant == 1) return launch<1>(ctx, a, b, r, out_min, out_argmin, n);
+    return launch<2>(ctx, a, b, r, out_min, out_argmin, n);
 }
