@@ -210,6 +210,23 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e = None if args.no_e2e else run_e2e(ctx, s, dev, stream, args, cap)
+    del pairs, flush
+
+    # the batched (64 uneven frames) and served (Poisson jobs) forms, 1 GPU only
+    batched = served = None
+    if ws == 1 and (args.batch_frames > 0):
+        import synth
+        frames = upload_frames(ctx, synth.batch_frames(args.batch_frames), dev)
+        with torch.cuda.stream(stream):
+            batched = run_batched(ctx, frames, stream, dev)
+            if args.served_jobs > 0:
+                served = {"config": run_served(ctx, frames, stream, dev, args.served_jobs, 200.0)}
+                # the same at a load the GPU can sustain: 70% of its job-by-job capacity
+                cap_jobs = args.batch_frames / (batched["plain_job_by_job"]["ms"] / 1e3)
+                served["sustainable"] = run_served(ctx, frames, stream, dev, max(16, args.served_jobs // 4),
+                                                   0.7 * cap_jobs, seed=12)
+        for fr in frames:
+            fr["tree"].free()
 
     result = None
     if rank == 0:
@@ -228,6 +245,8 @@ def run_ours(args):
             "wall_s": wall,
             "roofline": roof,
             "e2e": e2e,
+            "batched": batched,
+            "served": served,
             "gpu_launches": int(launches),
             "clocks": clk,
         }
@@ -348,6 +367,153 @@ def run_e2e(ctx, s, dev, stream, args, cap):
 
 
 # ---------------------------------------------------------------------------------------
+# batched and served forms
+# ---------------------------------------------------------------------------------------
+
+def upload_frames(ctx, frames_np, dev):
+    """Device copies of the batched workload's frames, each with a resident hierarchy and
+    tile (the served form keeps exactly these resident across jobs)."""
+    import numpy as np
+    import torch
+    out = []
+    for s in frames_np:
+        lp = torch.from_numpy(s.light_pos).to(dev)
+        ep = torch.from_numpy(s.eye_pos).to(dev)
+        L = [lp[:, k].contiguous() for k in range(3)] + [torch.from_numpy(s.intensity).to(dev)]
+        tree = ctx.build_light_tree(*L)
+        out.append({"x": ep[:, 0].contiguous(), "y": ep[:, 1].contiguous(), "z": ep[:, 2].contiguous(),
+                    "px": torch.from_numpy(s.px.view(np.int16)).to(dev),
+                    "py": torch.from_numpy(s.py.view(np.int16)).to(dev),
+                    "tree": tree, "tau": float(s.tau), "tile_np": s.tile,
+                    "tile": torch.from_numpy(np.ascontiguousarray(s.tile).view(np.int32)).to(dev),
+                    "n_e": len(s.eye_pos), "n_l": len(s.light_pos)})
+    torch.cuda.synchronize(dev)
+    return out
+
+
+def plain_frame(ctx, fr, pairs, stream):
+    """One frame through hrr_cull on the context stream: (ms on the device, count)."""
+    import torch
+    import paper_1907_12343_gb300 as hrr
+    ctx.set_shift_tile(fr["tile_np"])
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    st, cnt = ctx.cull(fr["x"], fr["y"], fr["z"], fr["px"], fr["py"], fr["tree"], fr["tau"], pairs)
+    b.record(stream)
+    b.synchronize()
+    if st != hrr.HRR_OK:
+        raise RuntimeError(f"plain cull status {st}")
+    return a.elapsed_time(b), cnt
+
+
+def run_batched(ctx, frames, stream, dev, runs=3):
+    """All frames in one persistent launch replayed from a CUDA graph, against the same
+    frames culled one hrr_cull call after another."""
+    import torch
+    import paper_1907_12343_gb300 as hrr
+    total_pairs = sum(fr["n_e"] * fr["n_l"] for fr in frames)
+    scratch = torch.empty((max(fr["n_e"] for fr in frames) * 200, 2), dtype=torch.int32, device=dev)
+    plain_ms, counts = [], []
+    for fr in frames:
+        ms, cnt = plain_frame(ctx, fr, scratch, stream)
+        plain_ms.append(ms)
+        counts.append(cnt)
+    del scratch
+    for fr, cnt in zip(frames, counts):
+        fr["count"] = cnt
+        fr["pairs"] = torch.empty((cnt + 1024, 2), dtype=torch.int32, device=dev)
+    b = hrr.Batch(ctx, frames, use_graph=True)
+    b.launch()
+    st, got, _ = b.results()
+    if st != hrr.HRR_OK or got != counts:
+        raise RuntimeError("batched counts differ from plain counts")
+    times = []
+    for _ in range(runs):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.launch()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        b.results()
+    b.destroy()
+    t_b = statistics.median(times) / 1e3
+    t_p = sum(plain_ms) / 1e3
+    return {"frames": len(frames), "eyes": sum(fr["n_e"] for fr in frames),
+            "lights": sum(fr["n_l"] for fr in frames), "accepted_pairs": int(sum(counts)),
+            "value": total_pairs / t_b, "unit": UNIT, "ms": t_b * 1e3, "graph": True,
+            "plain_job_by_job": {"value": total_pairs / t_p, "ms": t_p * 1e3},
+            "speedup_vs_plain": t_p / t_b}
+
+
+def _latency_stats(lat):
+    import numpy as np
+    a = np.sort(np.asarray(lat))
+    return {"p50_s": float(np.percentile(a, 50)), "p99_s": float(np.percentile(a, 99)),
+            "max_s": float(a[-1])}
+
+
+def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30):
+    """Poisson arrivals of frame-sized jobs against resident hierarchies and tiles, served
+    with continuous batching, against the same arrival sequence processed job by job."""
+    import threading as th
+    import numpy as np
+    import torch
+    import synth
+    import paper_1907_12343_gb300 as hrr
+    gaps = -np.log(1.0 - synth.uniform01(seed, 50, n_jobs)) / rate
+    arrive = np.cumsum(gaps) - gaps[0]
+    which = np.minimum((synth.uniform01(seed, 51, n_jobs) * len(frames)).astype(int), len(frames) - 1)
+    work = sum(frames[f]["n_e"] * frames[f]["n_l"] for f in which)
+
+    # served
+    srv = hrr.Server(ctx, budget, slice_eyes=1 << 19, max_jobs=max(64, n_jobs))
+    tickets = [None] * n_jobs
+    t0 = time.perf_counter()
+
+    def submitter():
+        for k in range(n_jobs):
+            dt = t0 + arrive[k] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            fr = frames[which[k]]
+            tickets[k] = srv.submit(fr["x"], fr["y"], fr["z"], fr["px"], fr["py"], fr["tree"], fr["tau"],
+                                    fr["count"] + 1024, tile=fr["tile"])
+
+    thr = th.Thread(target=submitter)
+    thr.start()
+    lat, mismatch = [], 0
+    for k in range(n_jobs):
+        while tickets[k] is None:
+            time.sleep(0.0005)
+        r = srv.wait(tickets[k], 3600.0)
+        if r["status"] != hrr.HRR_OK or r["count"] != frames[which[k]]["count"]:
+            mismatch += 1
+        lat.append(r["latency_s"])
+        srv.release(tickets[k])
+    thr.join()
+    makespan = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.destroy()
+
+    # plain, job by job in arrival order on the same GPU
+    scratch = torch.empty((max(fr["count"] for fr in frames) + 1024, 2), dtype=torch.int32, device=dev)
+    lat_p = []
+    t0 = time.perf_counter()
+    for k in range(n_jobs):
+        dt = t0 + arrive[k] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        plain_frame(ctx, frames[which[k]], scratch, stream)
+        lat_p.append(time.perf_counter() - t0 - arrive[k])
+    makespan_p = time.perf_counter() - t0
+    return {"jobs": n_jobs, "rate_per_s": rate, "hbm_budget_gb": budget / 2**30,
+            "value": work / makespan, "unit": UNIT, "latency": _latency_stats(lat),
+            "max_active": stats["max_active"], "slices": stats["slices"], "mismatched_jobs": mismatch,
+            "plain_job_by_job": {"value": work / makespan_p, "latency": _latency_stats(lat_p)}}
+
+
+# ---------------------------------------------------------------------------------------
 # the oracle on the host cores
 # ---------------------------------------------------------------------------------------
 
@@ -430,6 +596,8 @@ def main(argv=None):
     ap.add_argument("--eyes", default="1920x1080", help="frame size WxH (one eye per pixel)")
     ap.add_argument("--lights", type=int, default=1 << 20)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-frames", type=int, default=64, help="0 skips the batched/served forms")
+    ap.add_argument("--served-jobs", type=int, default=256, help="0 skips the served form")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -53,7 +53,8 @@ typedef enum hrr_status {
     HRR_ERR_OVERFLOW = 4,    /* output capacity too small; *out_count holds the need */
     HRR_ERR_TIMEOUT = 5,     /* a bounded device wait or queue wait ran out */
     HRR_ERR_CUDA = 6,        /* a CUDA runtime call failed */
-    HRR_ERR_DEVICE = 7       /* a kernel reported an internal error flag */
+    HRR_ERR_DEVICE = 7,      /* a kernel reported an internal error flag */
+    HRR_PENDING = 8          /* a served job has not finished yet (not an error) */
 } hrr_status;
 
 typedef struct hrr_ctx hrr_ctx;   /* opaque, library-owned */
@@ -202,6 +203,108 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
 /* Statistics of the last hrr_cull/hrr_cull_ex on this context: total internal-node
  * visits and accepted pairs (both exact, computed on the device). */
 int hrr_last_cull_stats(const hrr_ctx *ctx, uint64_t *visits, uint64_t *accepted);
+
+/* ---- batched culling (many frames in one persistent launch) ---------------------------- */
+
+/* One frame of a batch: its eyes, hierarchy, shifts, culling scale and output. Pairs are
+ * written as (eye index within the frame, original light id), as in hrr_cull. */
+typedef struct hrr_frame {
+    hrr_eyes eyes;              /* device SoA, n_eyes entries */
+    uint32_t n_eyes;            /* may be 0 */
+    const hrr_tree *tree;       /* built on the batch's context device */
+    const uint32_t *dev_tile;   /* device tile_w x tile_h shifts, or NULL for the context tile */
+    uint32_t tile_w, tile_h;
+    float tau;                  /* finite, >= 0 */
+    uint32_t shift_offset;      /* as in hrr_cull_opts */
+    uint32_t *dev_pairs;        /* 2 * cap uint32 of device memory, 8-byte aligned */
+    uint64_t cap;
+    uint32_t *eye_visits;       /* optional per-eye visit counts (device, n_eyes), or NULL */
+} hrr_frame;
+
+typedef struct hrr_batch hrr_batch; /* opaque, library-owned */
+
+/* Prepare a batch of 1..65535 frames for repeated culling: validates the frames, uploads
+ * their descriptors and per-frame counters to the device and, when use_graph != 0, records
+ * the launch (counter reset + one persistent traversal over every frame's eyes) into a
+ * CUDA graph. The frames' memory must stay valid while the batch exists. Synchronous.
+ * Status HRR_ERR_NO_TILE if a frame has no tile and the context has none. */
+int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames,
+                     int rangemin_variant, int use_graph, hrr_batch **out);
+/* Enqueue one run of the batch on the context stream (a graph replay when recorded).
+ * Asynchronous. */
+int hrr_batch_launch(hrr_ctx *ctx, hrr_batch *batch);
+/* Wait for the last run and copy its per-frame accepted-pair counts and node visits to
+ * host arrays of n_frames (either may be NULL). HRR_ERR_OVERFLOW if any frame's count
+ * exceeds its cap (its count is still reported). */
+int hrr_batch_results(hrr_ctx *ctx, hrr_batch *batch, uint64_t *counts, uint64_t *visits);
+/* Wait for the context stream and release the batch. */
+int hrr_batch_destroy(hrr_ctx *ctx, hrr_batch *batch);
+/* One-shot batch: create (no graph), launch, results, destroy. */
+int hrr_cull_batch(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames,
+                   int rangemin_variant, uint64_t *counts);
+
+/* ---- served culling (continuous batching) --------------------------------------------- */
+
+/* A culling job: eyes against a device-resident hierarchy and tile. The server reserves
+ * cap output pairs for it. All pointers must stay valid until the job is released. */
+typedef struct hrr_job {
+    hrr_eyes eyes;              /* device SoA */
+    uint32_t n_eyes;
+    const hrr_tree *tree;       /* built on the server's device, kept resident by the caller */
+    const uint32_t *dev_tile;   /* device tile, or NULL for the submitting context's tile */
+    uint32_t tile_w, tile_h;
+    float tau;
+    uint32_t shift_offset;
+    uint64_t cap;               /* output pairs to reserve */
+} hrr_job;
+
+typedef struct hrr_job_result {
+    int status;                 /* HRR_PENDING, HRR_OK, HRR_ERR_OVERFLOW (count > cap; the
+                                   buffer holds cap of the pairs), HRR_ERR_OOM (the job's
+                                   reservation exceeds the budget), HRR_ERR_DEVICE */
+    uint64_t count;             /* accepted pairs */
+    uint64_t visits;            /* internal-node visits */
+    const uint32_t *dev_pairs;  /* server-owned device buffer of min(count, cap) pairs
+                                   (eye index within the job, original light id), valid
+                                   until hrr_server_release */
+    double queue_s;             /* submission to admission (so far, while waiting) */
+    double latency_s;           /* submission to completion (so far, while pending) */
+} hrr_job_result;
+
+typedef struct hrr_server_info {
+    uint64_t slices, launches, jobs_done, jobs_waiting, jobs_active, bytes_reserved;
+    uint32_t max_active;        /* most jobs admitted at once so far */
+} hrr_server_info;
+
+typedef struct hrr_server hrr_server; /* opaque, library-owned */
+
+/* Start a server on ctx's device with its own stream and scheduler thread. Jobs are
+ * admitted in arrival order while their output reservations (cap * 8 bytes) fit in
+ * hbm_budget_bytes and fewer than max_jobs are admitted; the GPU then runs slices, each
+ * one batched traversal over up to slice_eyes (0: 2^19) of the admitted jobs' remaining
+ * eyes, oldest job first, so jobs arriving while others run join a slice as soon as the
+ * older jobs leave room. Each job's result is exactly what hrr_cull would produce for it
+ * alone. The server never makes the GPU wait on the host. rangemin_variant as in
+ * hrr_cull_opts. */
+int hrr_server_create(hrr_ctx *ctx, uint64_t hbm_budget_bytes, uint32_t slice_eyes,
+                      uint32_t max_jobs, int rangemin_variant, hrr_server **out);
+/* Queue a job (thread-safe, non-blocking); *ticket identifies it. ctx (may be NULL when the
+ * job has its own tile) receives the error text of a rejected job. */
+int hrr_server_submit(hrr_server *server, hrr_ctx *ctx, const hrr_job *job, uint64_t *ticket);
+/* HRR_OK with the result when the job has finished, HRR_PENDING otherwise (non-blocking). */
+int hrr_server_poll(hrr_server *server, uint64_t ticket, hrr_job_result *result);
+/* Block until the job finishes (HRR_OK) or timeout_s passes (HRR_ERR_TIMEOUT). */
+int hrr_server_wait(hrr_server *server, uint64_t ticket, double timeout_s, hrr_job_result *result);
+/* Copy up to max_pairs of a finished job's pairs (min(count, cap) are stored) to host
+ * memory; *copied receives the number copied. Synchronous. */
+int hrr_server_copy_pairs(hrr_server *server, uint64_t ticket, uint32_t *host_pairs,
+                          uint64_t max_pairs, uint64_t *copied);
+/* Free a finished job's output buffer and reservation; the ticket becomes invalid. */
+int hrr_server_release(hrr_server *server, uint64_t ticket);
+/* Counters of the scheduler. */
+int hrr_server_stats(hrr_server *server, hrr_server_info *info);
+/* Finish every submitted job, stop the scheduler and free everything the server owns. */
+int hrr_server_destroy(hrr_server *server);
 
 /* ---- range minimum (Sec. 2, Alg. 1-3) -------------------------------------------------- */
 

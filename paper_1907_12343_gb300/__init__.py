@@ -32,6 +32,7 @@ HRR_ERR_OVERFLOW = 4
 HRR_ERR_TIMEOUT = 5
 HRR_ERR_CUDA = 6
 HRR_ERR_DEVICE = 7
+HRR_PENDING = 8
 
 
 class hrr_lights(C.Structure):
@@ -55,6 +56,30 @@ assert C.sizeof(hrr_node) == 64
 NODE_DTYPE = np.dtype([("c0_lo", "<f4", 3), ("c0_imax", "<f4"), ("c0_hi", "<f4", 3),
                        ("split", "<u4"), ("c1_lo", "<f4", 3), ("c1_imax", "<f4"),
                        ("c1_hi", "<f4", 3), ("other_end", "<u4")])
+
+
+class hrr_frame(C.Structure):
+    _fields_ = [("eyes", hrr_eyes), ("n_eyes", C.c_uint32), ("tree", C.c_void_p),
+                ("dev_tile", C.c_void_p), ("tile_w", C.c_uint32), ("tile_h", C.c_uint32),
+                ("tau", C.c_float), ("shift_offset", C.c_uint32), ("dev_pairs", C.c_void_p),
+                ("cap", C.c_uint64), ("eye_visits", C.c_void_p)]
+
+
+class hrr_job(C.Structure):
+    _fields_ = [("eyes", hrr_eyes), ("n_eyes", C.c_uint32), ("tree", C.c_void_p),
+                ("dev_tile", C.c_void_p), ("tile_w", C.c_uint32), ("tile_h", C.c_uint32),
+                ("tau", C.c_float), ("shift_offset", C.c_uint32), ("cap", C.c_uint64)]
+
+
+class hrr_job_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("count", C.c_uint64), ("visits", C.c_uint64),
+                ("dev_pairs", C.c_void_p), ("queue_s", C.c_double), ("latency_s", C.c_double)]
+
+
+class hrr_server_info(C.Structure):
+    _fields_ = [("slices", C.c_uint64), ("launches", C.c_uint64), ("jobs_done", C.c_uint64),
+                ("jobs_waiting", C.c_uint64), ("jobs_active", C.c_uint64),
+                ("bytes_reserved", C.c_uint64), ("max_active", C.c_uint32)]
 
 
 class hrr_cull_opts(C.Structure):
@@ -85,6 +110,19 @@ _SIGS = {
     "hrr_range_min": (_i32, [_P, _P, _P, _P, _P, _P, _u64, _i32]),
     "hrr_build_light_tree_static": (_i32, [hrr_lights, _u32, _P, _P, C.POINTER(_u32), _P,
                                            C.c_char_p, C.c_size_t]),
+    "hrr_batch_create": (_i32, [_P, C.POINTER(hrr_frame), _u32, _i32, _i32, C.POINTER(_P)]),
+    "hrr_batch_launch": (_i32, [_P, _P]),
+    "hrr_batch_results": (_i32, [_P, _P, C.POINTER(_u64), C.POINTER(_u64)]),
+    "hrr_batch_destroy": (_i32, [_P, _P]),
+    "hrr_cull_batch": (_i32, [_P, C.POINTER(hrr_frame), _u32, _i32, C.POINTER(_u64)]),
+    "hrr_server_create": (_i32, [_P, _u64, _u32, _u32, _i32, C.POINTER(_P)]),
+    "hrr_server_submit": (_i32, [_P, _P, C.POINTER(hrr_job), C.POINTER(_u64)]),
+    "hrr_server_poll": (_i32, [_P, _u64, C.POINTER(hrr_job_result)]),
+    "hrr_server_wait": (_i32, [_P, _u64, C.c_double, C.POINTER(hrr_job_result)]),
+    "hrr_server_release": (_i32, [_P, _u64]),
+    "hrr_server_stats": (_i32, [_P, C.POINTER(hrr_server_info)]),
+    "hrr_server_destroy": (_i32, [_P]),
+    "hrr_server_copy_pairs": (_i32, [_P, _u64, _P, _u64, C.POINTER(_u64)]),
 }
 STATIC_BUILD_MAX_LIGHTS = 65536
 for _name, (_res, _args) in _SIGS.items():
@@ -194,6 +232,135 @@ class Context:
         ms, n = C.c_double(), _u64()
         self.check(hrr_kernel_time(self.handle, C.byref(ms), C.byref(n)))
         return float(ms.value), int(n.value)
+
+
+class Batch:
+    """Frames culled together in one persistent launch (optionally a recorded CUDA graph).
+
+    ``frames`` is a list of dicts with keys: x, y, z, px, py (CUDA tensors of one frame's
+    eyes), tree (Tree), tau, pairs (int32 tensor (cap, 2)); optional tile (uint32 tensor
+    (h, w) on the device), shift_offset, eye_visits (int32 tensor)."""
+
+    def __init__(self, ctx: "Context", frames, rangemin_variant: int = 0, use_graph: bool = True):
+        self.ctx = ctx
+        self.n = len(frames)
+        arr = (hrr_frame * self.n)()
+        self._keep = frames  # the frames' tensors must outlive the batch
+        for i, fr in enumerate(frames):
+            tile = fr.get("tile")
+            arr[i] = hrr_frame(
+                hrr_eyes(_ptr(fr["x"]), _ptr(fr["y"]), _ptr(fr["z"]), _ptr(fr["px"]), _ptr(fr["py"])),
+                int(fr["x"].numel()), fr["tree"].handle,
+                _ptr(tile), int(tile.shape[1]) if tile is not None else 0,
+                int(tile.shape[0]) if tile is not None else 0,
+                float(fr["tau"]), int(fr.get("shift_offset", 0)),
+                _ptr(fr["pairs"]) if fr["pairs"].shape[0] else None, int(fr["pairs"].shape[0]),
+                _ptr(fr.get("eye_visits")))
+        h = _P()
+        ctx.check(hrr_batch_create(ctx.handle, arr, self.n, rangemin_variant, 1 if use_graph else 0,
+                                   C.byref(h)))
+        self.handle = h
+
+    def launch(self):
+        self.ctx.check(hrr_batch_launch(self.ctx.handle, self.handle))
+
+    def results(self):
+        """(status, counts, visits): HRR_ERR_OVERFLOW is returned, not raised."""
+        counts = (_u64 * self.n)()
+        visits = (_u64 * self.n)()
+        st = hrr_batch_results(self.ctx.handle, self.handle, counts, visits)
+        if st not in (HRR_OK, HRR_ERR_OVERFLOW):
+            self.ctx.check(st)
+        return st, [int(c) for c in counts], [int(v) for v in visits]
+
+    def destroy(self):
+        if self.handle:
+            self.ctx.check(hrr_batch_destroy(self.ctx.handle, self.handle))
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            if self.handle and self.ctx.handle:
+                self.destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """Served culling with continuous batching (a scheduler thread inside the library).
+
+    Jobs are eyes (CUDA tensors) against a resident Tree; submit() returns a ticket at once,
+    wait()/poll() give the result, release() frees the job's output buffer."""
+
+    def __init__(self, ctx: "Context", hbm_budget_bytes: int, slice_eyes: int = 0,
+                 max_jobs: int = 1024, rangemin_variant: int = 0):
+        self.ctx = ctx
+        h = _P()
+        ctx.check(hrr_server_create(ctx.handle, int(hbm_budget_bytes), int(slice_eyes), int(max_jobs),
+                                    rangemin_variant, C.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, x, y, z, px, py, tree: "Tree", tau: float, cap: int, tile=None,
+               shift_offset: int = 0) -> int:
+        job = hrr_job(hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py)), int(x.numel()),
+                      tree.handle, _ptr(tile), int(tile.shape[1]) if tile is not None else 0,
+                      int(tile.shape[0]) if tile is not None else 0, float(tau), int(shift_offset),
+                      int(cap))
+        t = _u64()
+        self.ctx.check(hrr_server_submit(self.handle, self.ctx.handle, C.byref(job), C.byref(t)))
+        self._keep[int(t.value)] = (x, y, z, px, py, tile)
+        return int(t.value)
+
+    @staticmethod
+    def _res(r):
+        return {"status": int(r.status), "count": int(r.count), "visits": int(r.visits),
+                "dev_pairs": r.dev_pairs, "queue_s": float(r.queue_s), "latency_s": float(r.latency_s)}
+
+    def poll(self, ticket: int):
+        r = hrr_job_result()
+        st = hrr_server_poll(self.handle, ticket, C.byref(r))
+        if st not in (HRR_OK, HRR_PENDING):
+            raise HRRError(st, "hrr_server_poll")
+        return self._res(r)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        r = hrr_job_result()
+        st = hrr_server_wait(self.handle, ticket, float(timeout_s), C.byref(r))
+        if st not in (HRR_OK, HRR_ERR_TIMEOUT):
+            raise HRRError(st, "hrr_server_wait")
+        out = self._res(r)
+        out["wait_status"] = st
+        return out
+
+    def pairs(self, ticket: int, result) -> np.ndarray:
+        """Copy a finished job's pairs to a host array of shape (n, 2), n <= count."""
+        n = int(result["count"])
+        out = np.empty((max(n, 1), 2), dtype=np.uint32)
+        got = _u64()
+        self.ctx.check(hrr_server_copy_pairs(self.handle, ticket, out.ctypes.data, n, C.byref(got)))
+        return out[:int(got.value)]
+
+    def release(self, ticket: int):
+        self.ctx.check(hrr_server_release(self.handle, ticket))
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        i = hrr_server_info()
+        self.ctx.check(hrr_server_stats(self.handle, C.byref(i)))
+        return {k: int(getattr(i, k)) for k, _ in hrr_server_info._fields_}
+
+    def destroy(self):
+        if self.handle:
+            hrr_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 class Tree:

@@ -57,6 +57,7 @@ const char *hrr_status_string(int s) {
     case HRR_ERR_TIMEOUT: return "HRR_ERR_TIMEOUT";
     case HRR_ERR_CUDA: return "HRR_ERR_CUDA";
     case HRR_ERR_DEVICE: return "HRR_ERR_DEVICE";
+    case HRR_PENDING: return "HRR_PENDING";
     default: return "HRR_UNKNOWN_STATUS";
     }
 }

@@ -1,0 +1,201 @@
+// Batched culling: many frames (each its own eyes, hierarchy, tile, tau and output) in one
+// persistent traversal launch, optionally recorded once into a CUDA graph and replayed.
+//
+// A batch keeps its frame descriptors, per-frame counters and the launch's eye cursor in
+// device memory. Replaying it resets the counters and runs the traversal over the eyes of
+// every frame; frames of very different sizes share the launch, so there is no per-frame
+// launch overhead or tail.
+#include <new>
+#include <vector>
+
+#include "hrr_internal.cuh"
+
+struct hrr_batch {
+    uint32_t n_frames = 0;
+    unsigned long long total = 0;
+    int variant = 0;
+    hrr_cull_frame_t *dev_frames = nullptr;
+    unsigned long long *dev_counts = nullptr;  // 2 per frame (accepted, visits), then cursor, flags
+    unsigned long long *host_counts = nullptr; // pinned mirror
+    std::vector<uint64_t> caps;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+int enqueue(hrr_ctx *ctx, hrr_batch *b, cudaStream_t st) {
+    const size_t bytes = sizeof(unsigned long long) * (2 * (size_t)b->n_frames + 2);
+    HRR_CUDA(ctx, cudaMemsetAsync(b->dev_counts, 0, bytes, st));
+    unsigned long long *misc = b->dev_counts + 2 * (size_t)b->n_frames;
+    HRR_CUDA(ctx, hrr_cull_batch_enqueue(ctx->sm_count, b->dev_frames, b->n_frames, b->total, misc,
+                                         misc + 1, b->variant, st));
+    if (b->total) ++ctx->launches;
+    return HRR_OK;
+}
+
+void release(hrr_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->dev_frames) cudaFree(b->dev_frames);
+    if (b->dev_counts) cudaFree(b->dev_counts);
+    if (b->host_counts) cudaFreeHost(b->host_counts);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, int rangemin_variant,
+                     int use_graph, hrr_batch **out) {
+    if (!ctx) return HRR_ERR_INVALID_ARG;
+    if (!out) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!frames || n_frames == 0 || n_frames > 65535)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "n_frames must be in [1, 65535]");
+    if (rangemin_variant < 0 || rangemin_variant > 2)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2");
+    std::vector<hrr_cull_frame_t> desc(n_frames);
+    hrr_batch *b = new (std::nothrow) hrr_batch();
+    if (!b) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of the batch");
+    b->n_frames = n_frames;
+    b->variant = rangemin_variant;
+    b->caps.resize(n_frames);
+    DeviceGuard g(ctx->device);
+    unsigned long long cursor = 0;
+    for (uint32_t i = 0; i < n_frames; ++i) {
+        const hrr_frame &fr = frames[i];
+        const char *bad = nullptr;
+        int status = HRR_ERR_INVALID_ARG;
+        if (!fr.tree || fr.tree->device != ctx->device) bad = "a frame's tree is NULL or on another device";
+        else if (!(fr.tau >= 0.0f) || !(fr.tau < __builtin_huge_valf())) bad = "a frame's tau is not finite and >= 0";
+        else if (fr.n_eyes && (!fr.eyes.x || !fr.eyes.y || !fr.eyes.z || !fr.eyes.px || !fr.eyes.py))
+            bad = "a frame's eye array is NULL";
+        else if (fr.cap && !fr.dev_pairs) bad = "a frame's dev_pairs is NULL";
+        else if (((uintptr_t)fr.dev_pairs & 7u) != 0) bad = "a frame's dev_pairs is not 8-byte aligned";
+        else if (fr.dev_tile && (fr.tile_w == 0 || fr.tile_h == 0 || fr.tile_w > 65536 || fr.tile_h > 65536))
+            bad = "a frame's tile size is invalid";
+        else if (!fr.dev_tile && !ctx->tile) {
+            bad = "a frame has no tile and no context tile is set";
+            status = HRR_ERR_NO_TILE;
+        }
+        if (bad) {
+            release(b);
+            return hrr_fail(ctx, status, bad);
+        }
+        hrr_cull_frame_t &d = desc[i];
+        d = hrr_cull_frame_t{};
+        d.ex = fr.eyes.x; d.ey = fr.eyes.y; d.ez = fr.eyes.z; d.px = fr.eyes.px; d.py = fr.eyes.py;
+        d.nodes = reinterpret_cast<const float4 *>(fr.tree->nodes);
+        d.perm = fr.tree->perm;
+        d.tile = fr.dev_tile ? fr.dev_tile : ctx->tile;
+        d.tile_w = fr.dev_tile ? fr.tile_w : ctx->tile_w;
+        d.tile_h = fr.dev_tile ? fr.tile_h : ctx->tile_h;
+        d.pairs = reinterpret_cast<uint2 *>(fr.dev_pairs);
+        d.cap = fr.cap;
+        d.eye_visits = fr.eye_visits;
+        d.n_lights = fr.tree->n;
+        d.shift_offset = fr.shift_offset;
+        d.tau = fr.tau;
+        d.eye_begin = 0;
+        d.cursor_begin = cursor;
+        cursor += fr.n_eyes;
+        b->caps[i] = fr.cap;
+    }
+    b->total = cursor;
+    cudaError_t e = cudaMalloc(&b->dev_frames, sizeof(hrr_cull_frame_t) * n_frames);
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_counts, sizeof(unsigned long long) * (2 * (size_t)n_frames + 2));
+    if (e == cudaSuccess) e = cudaMallocHost(&b->host_counts, sizeof(unsigned long long) * (2 * (size_t)n_frames + 2));
+    if (e != cudaSuccess) {
+        release(b);
+        return hrr_cuda_fail(ctx, e, "batch allocation");
+    }
+    for (uint32_t i = 0; i < n_frames; ++i) desc[i].counts = b->dev_counts + 2 * (size_t)i;
+    e = cudaMemcpy(b->dev_frames, desc.data(), sizeof(hrr_cull_frame_t) * n_frames, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        release(b);
+        return hrr_cuda_fail(ctx, e, "batch descriptor upload");
+    }
+    if (use_graph) {
+        // Record [reset counters, traversal] once on a private stream; replays go to ctx->stream.
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const uint64_t launches = ctx->launches;
+            const int st = enqueue(ctx, b, b->capture_stream);
+            ctx->launches = launches;  // recording is not a launch
+            const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &graph);
+            e = st != HRR_OK ? cudaErrorUnknown : e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            release(b);
+            return hrr_cuda_fail(ctx, e, "batch graph capture");
+        }
+    }
+    *out = b;
+    return HRR_OK;
+}
+
+int hrr_batch_launch(hrr_ctx *ctx, hrr_batch *b) {
+    if (!ctx || !b) return HRR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (b->exec) {
+        HRR_CUDA(ctx, cudaGraphLaunch(b->exec, ctx->stream));
+        ++ctx->launches;
+        return HRR_OK;
+    }
+    return enqueue(ctx, b, ctx->stream);
+}
+
+int hrr_batch_results(hrr_ctx *ctx, hrr_batch *b, uint64_t *counts, uint64_t *visits) {
+    if (!ctx || !b) return HRR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    const size_t n = 2 * (size_t)b->n_frames + 2;
+    HRR_CUDA(ctx, cudaMemcpyAsync(b->host_counts, b->dev_counts, sizeof(unsigned long long) * n,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    HRR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    bool overflow = false;
+    uint64_t acc = 0, vis = 0;
+    for (uint32_t i = 0; i < b->n_frames; ++i) {
+        const uint64_t c = b->host_counts[2 * (size_t)i];
+        if (counts) counts[i] = c;
+        if (visits) visits[i] = b->host_counts[2 * (size_t)i + 1];
+        if (c > b->caps[i]) overflow = true;
+        acc += c;
+        vis += b->host_counts[2 * (size_t)i + 1];
+    }
+    ctx->last_accepted = acc;
+    ctx->last_visits = vis;
+    const unsigned long long flags = b->host_counts[n - 1];
+    if (flags & HRR_FLAG_STACK) return hrr_fail(ctx, HRR_ERR_DEVICE, "traversal stack overflow");
+    if (flags & HRR_FLAG_TOPOLOGY) return hrr_fail(ctx, HRR_ERR_DEVICE, "corrupt node record");
+    if (overflow) return hrr_fail(ctx, HRR_ERR_OVERFLOW, "a frame's output capacity is too small");
+    return HRR_OK;
+}
+
+int hrr_batch_destroy(hrr_ctx *ctx, hrr_batch *b) {
+    if (!ctx || !b) return HRR_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    release(b);
+    return HRR_OK;
+}
+
+int hrr_cull_batch(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, int rangemin_variant,
+                   uint64_t *counts) {
+    hrr_batch *b = nullptr;
+    int st = hrr_batch_create(ctx, frames, n_frames, rangemin_variant, 0, &b);
+    if (st != HRR_OK) return st;
+    st = hrr_batch_launch(ctx, b);
+    if (st == HRR_OK) st = hrr_batch_results(ctx, b, counts, nullptr);
+    const std::string err = ctx->err;
+    hrr_batch_destroy(ctx, b);
+    ctx->err = err;
+    return st;
+}
+
+}  // extern "C"

@@ -66,6 +66,30 @@ struct DeviceGuard {
     }
 };
 
+// One frame of a traversal launch, as the kernel reads it (hrr_cull.cu): a single frame
+// for hrr_cull, an array of them for batches. 128 bytes.
+struct hrr_cull_frame_t {
+    const float *ex, *ey, *ez;
+    const uint16_t *px, *py;
+    const float4 *nodes;
+    const uint32_t *perm;
+    const uint32_t *tile;
+    uint2 *pairs;
+    unsigned long long cap;
+    unsigned long long *counts;      // [0] accepted pairs, [1] node visits
+    uint32_t *eye_visits;            // optional per-eye visit counts
+    uint32_t n_lights, tile_w, tile_h, shift_offset;
+    float tau;
+    uint32_t eye_begin;              // first eye of the frame covered by this launch
+    unsigned long long cursor_begin; // where the frame's eyes start on the launch's cursor
+};
+
+// Enqueue one batched traversal on st (hrr_cull.cu); a no-op when total == 0. The cursor
+// must be zero when the kernel starts. sm_count sizes the persistent grid.
+cudaError_t hrr_cull_batch_enqueue(int sm_count, const hrr_cull_frame_t *dev_frames, uint32_t n_frames,
+                                   unsigned long long total, unsigned long long *cursor,
+                                   unsigned long long *flags, int variant, cudaStream_t st);
+
 // Traversal timing (hrr_abi.cu)
 void hrr_timing_begin(hrr_ctx *ctx);
 void hrr_timing_end(hrr_ctx *ctx);

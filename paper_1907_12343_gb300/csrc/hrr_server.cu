@@ -1,0 +1,472 @@
+// Served culling with continuous batching.
+//
+// Clients submit culling jobs (a set of eyes against a device-resident light hierarchy and
+// shift tile) from any thread. A scheduler thread owned by the server:
+//   * admits waiting jobs in arrival order while their output reservation fits the HBM
+//     budget, giving each a slot of device counters and an output buffer;
+//   * runs the GPU as a sequence of slices: each slice is one persistent batched traversal
+//     over up to slice_eyes of the admitted jobs' remaining eyes, oldest job first, so a
+//     job that arrives while others are on the GPU joins a slice as soon as the older jobs
+//     leave room, and its work overlaps theirs;
+//   * keeps at most kRing slices enqueued, so admission reacts within about one slice;
+//   * completes a job when the slice holding its last eyes finishes, publishing its pair
+//     count and node visits.
+// The device never waits on the host: all scheduling happens between launches, so no
+// kernel spins on a queue and nothing can hang a GPU. A job's result is independent of
+// which other jobs shared its slices (each frame of a slice is traversed exactly as
+// hrr_cull would).
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "hrr_internal.cuh"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr int kRing = 2;  // slices enqueued at once (one running, one waiting)
+
+struct Job {
+    uint64_t ticket = 0;
+    hrr_job desc{};
+    const uint32_t *tile = nullptr;
+    uint32_t tile_w = 0, tile_h = 0;
+    int slot = -1;
+    uint2 *pairs = nullptr;
+    uint64_t bytes = 0;
+    uint32_t next_eye = 0;
+    bool admitted = false;
+    bool all_launched = false;
+    bool done = false;
+    cudaEvent_t done_ev = nullptr;
+    int status = HRR_PENDING;
+    uint64_t count = 0, visits = 0;
+    Clock::time_point t_submit, t_admit, t_done;
+};
+
+}  // namespace
+
+struct hrr_server {
+    int device = 0, sm_count = 0, variant = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0, used = 0;
+    uint32_t slice_eyes = 0, max_slots = 0;
+    unsigned long long *dev_counts = nullptr;   // 2 per slot: accepted, visits
+    unsigned long long *host_counts = nullptr;  // pinned copies, 2 per slot
+    hrr_cull_frame_t *dev_frames[kRing] = {};
+    hrr_cull_frame_t *host_frames[kRing] = {};  // pinned staging of slice descriptors
+    unsigned long long *dev_misc = nullptr;     // 2 per ring entry: cursor, flags
+    unsigned long long *host_flags = nullptr;   // pinned, 1 per ring entry
+    cudaEvent_t slice_done[kRing] = {};
+    bool slice_busy[kRing] = {};
+    std::vector<Job *> slice_jobs[kRing];
+    std::vector<int> free_slots;
+    std::deque<Job *> pending;
+    std::vector<Job *> active;
+    std::map<uint64_t, Job *> jobs;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread thread;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    uint64_t launches = 0, slices = 0, jobs_done = 0;
+    uint32_t max_active = 0;
+    std::string err;
+};
+
+namespace {
+
+double seconds(Clock::duration d) { return std::chrono::duration<double>(d).count(); }
+
+// Finish every job whose last slice has completed, and free finished slice entries.
+void reap(hrr_server *s) {
+    for (int k = 0; k < kRing; ++k) {
+        if (s->slice_busy[k] && cudaEventQuery(s->slice_done[k]) == cudaSuccess) {
+            s->slice_busy[k] = false;
+            if (s->host_flags[k])
+                for (Job *j : s->slice_jobs[k]) j->status = HRR_ERR_DEVICE;
+            s->slice_jobs[k].clear();
+        }
+    }
+    for (size_t i = 0; i < s->active.size();) {
+        Job *j = s->active[i];
+        if (j->all_launched && cudaEventQuery(j->done_ev) == cudaSuccess) {
+            j->count = s->host_counts[2 * (size_t)j->slot];
+            j->visits = s->host_counts[2 * (size_t)j->slot + 1];
+            if (j->status == HRR_PENDING) j->status = j->count > j->desc.cap ? HRR_ERR_OVERFLOW : HRR_OK;
+            j->t_done = Clock::now();
+            j->done = true;
+            s->free_slots.push_back(j->slot);
+            j->slot = -1;
+            s->active.erase(s->active.begin() + (long)i);  // keep admission order
+            ++s->jobs_done;
+            s->cv_done.notify_all();
+        } else {
+            ++i;
+        }
+    }
+}
+
+void fail_job(hrr_server *s, Job *j, int status) {
+    j->status = status;
+    j->done = true;
+    j->t_done = Clock::now();
+    ++s->jobs_done;
+    s->cv_done.notify_all();
+}
+
+// Admit waiting jobs in arrival order while a slot is free and their output fits.
+void admit(hrr_server *s) {
+    while (!s->pending.empty() && !s->free_slots.empty()) {
+        Job *j = s->pending.front();
+        if (j->bytes > s->budget) {  // can never fit
+            s->pending.pop_front();
+            fail_job(s, j, HRR_ERR_OOM);
+            continue;
+        }
+        if (s->used + j->bytes > s->budget) break;
+        void *p = nullptr;
+        if (j->bytes && cudaMallocAsync(&p, j->bytes, s->stream) != cudaSuccess) {
+            cudaGetLastError();
+            if (s->active.empty()) {  // nothing will free memory: give up on this job
+                s->pending.pop_front();
+                fail_job(s, j, HRR_ERR_OOM);
+                continue;
+            }
+            break;
+        }
+        s->pending.pop_front();
+        j->pairs = static_cast<uint2 *>(p);
+        s->used += j->bytes;
+        j->slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        cudaMemsetAsync(s->dev_counts + 2 * (size_t)j->slot, 0, 2 * sizeof(unsigned long long), s->stream);
+        j->t_admit = Clock::now();
+        j->admitted = true;
+        s->active.push_back(j);
+        if (s->active.size() > s->max_active) s->max_active = (uint32_t)s->active.size();
+    }
+}
+
+// Enqueue one slice: up to slice_eyes of the admitted jobs' remaining eyes, taken in
+// admission order (the oldest job first). Each job thus finishes as early as its place in
+// the queue allows, the next jobs' eyes fill the GPU while the older ones drain, and only a
+// few hierarchies are live in L2 at a time. Returns false when there was nothing to do.
+bool enqueue_slice(hrr_server *s, int k) {
+    std::vector<Job *> work;
+    std::vector<uint32_t> takes;
+    uint64_t budget = s->slice_eyes;
+    for (Job *j : s->active) {
+        if (j->all_launched) continue;
+        if (budget == 0) break;
+        const uint32_t take = (uint32_t)std::min<uint64_t>(budget, j->desc.n_eyes - j->next_eye);
+        work.push_back(j);
+        takes.push_back(take);
+        budget -= take;
+    }
+    if (work.empty()) return false;
+    hrr_cull_frame_t *h = s->host_frames[k];
+    unsigned long long cursor = 0;
+    uint32_t n = 0;
+    std::vector<Job *> finishing;
+    for (size_t w = 0; w < work.size(); ++w) {
+        Job *j = work[w];
+        const uint32_t take = takes[w];
+        hrr_cull_frame_t &d = h[n++];
+        d = hrr_cull_frame_t{};
+        d.ex = j->desc.eyes.x; d.ey = j->desc.eyes.y; d.ez = j->desc.eyes.z;
+        d.px = j->desc.eyes.px; d.py = j->desc.eyes.py;
+        d.nodes = reinterpret_cast<const float4 *>(j->desc.tree->nodes);
+        d.perm = j->desc.tree->perm;
+        d.tile = j->tile; d.tile_w = j->tile_w; d.tile_h = j->tile_h;
+        d.pairs = j->pairs;
+        d.cap = j->desc.cap;
+        d.counts = s->dev_counts + 2 * (size_t)j->slot;
+        d.eye_visits = nullptr;
+        d.n_lights = j->desc.tree->n;
+        d.shift_offset = j->desc.shift_offset;
+        d.tau = j->desc.tau;
+        d.eye_begin = j->next_eye;
+        d.cursor_begin = cursor;
+        cursor += take;
+        j->next_eye += take;
+        if (j->next_eye == j->desc.n_eyes) finishing.push_back(j);
+    }
+    cudaMemcpyAsync(s->dev_frames[k], h, sizeof(hrr_cull_frame_t) * n, cudaMemcpyHostToDevice, s->stream);
+    cudaMemsetAsync(s->dev_misc + 2 * k, 0, 2 * sizeof(unsigned long long), s->stream);
+    if (hrr_cull_batch_enqueue(s->sm_count, s->dev_frames[k], n, cursor, s->dev_misc + 2 * k,
+                               s->dev_misc + 2 * k + 1, s->variant, s->stream) == cudaSuccess && cursor)
+        ++s->launches;
+    cudaMemcpyAsync(&s->host_flags[k], s->dev_misc + 2 * k + 1, sizeof(unsigned long long),
+                    cudaMemcpyDeviceToHost, s->stream);
+    for (Job *j : finishing) {
+        cudaMemcpyAsync(s->host_counts + 2 * (size_t)j->slot, s->dev_counts + 2 * (size_t)j->slot,
+                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream);
+        cudaEventRecord(j->done_ev, s->stream);
+        j->all_launched = true;
+    }
+    s->slice_jobs[k] = work;
+    cudaEventRecord(s->slice_done[k], s->stream);
+    s->slice_busy[k] = true;
+    ++s->slices;
+    return true;
+}
+
+void run(hrr_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        reap(s);
+        admit(s);
+        if (s->stop && s->pending.empty() && s->active.empty()) break;
+        int k = -1;
+        for (int i = 0; i < kRing; ++i)
+            if (!s->slice_busy[i]) { k = i; break; }
+        bool enqueued = false;
+        if (k >= 0) enqueued = enqueue_slice(s, k);
+        if (enqueued) continue;
+        // Nothing to enqueue now: wait for the oldest busy slice, or for new work.
+        int busy = -1;
+        for (int i = 0; i < kRing; ++i)
+            if (s->slice_busy[i]) { busy = i; break; }
+        bool finishing = false;
+        for (Job *j : s->active) finishing |= j->all_launched;
+        if (busy >= 0 || finishing) {
+            cudaEvent_t ev = busy >= 0 ? s->slice_done[busy] : nullptr;
+            lk.unlock();
+            if (ev) cudaEventSynchronize(ev);
+            else std::this_thread::sleep_for(std::chrono::microseconds(100));
+            lk.lock();
+        } else {
+            s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        }
+    }
+}
+
+void destroy_resources(hrr_server *s) {
+    for (auto &kv : s->jobs) {
+        Job *j = kv.second;
+        if (j->pairs) cudaFreeAsync(j->pairs, s->stream);
+        if (j->done_ev) cudaEventDestroy(j->done_ev);
+        delete j;
+    }
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (int k = 0; k < kRing; ++k) {
+        if (s->dev_frames[k]) cudaFree(s->dev_frames[k]);
+        if (s->host_frames[k]) cudaFreeHost(s->host_frames[k]);
+        if (s->slice_done[k]) cudaEventDestroy(s->slice_done[k]);
+    }
+    if (s->dev_counts) cudaFree(s->dev_counts);
+    if (s->host_counts) cudaFreeHost(s->host_counts);
+    if (s->dev_misc) cudaFree(s->dev_misc);
+    if (s->host_flags) cudaFreeHost(s->host_flags);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+void fill_result(const Job *j, hrr_job_result *r) {
+    if (!r) return;
+    r->status = j->done ? j->status : HRR_PENDING;
+    r->count = j->count;
+    r->visits = j->visits;
+    r->dev_pairs = reinterpret_cast<const uint32_t *>(j->pairs);
+    r->queue_s = j->admitted ? seconds(j->t_admit - j->t_submit)
+                             : (j->done ? seconds(j->t_done - j->t_submit) : seconds(Clock::now() - j->t_submit));
+    r->latency_s = j->done ? seconds(j->t_done - j->t_submit) : seconds(Clock::now() - j->t_submit);
+}
+
+}  // namespace
+
+extern "C" {
+
+int hrr_server_create(hrr_ctx *ctx, uint64_t hbm_budget_bytes, uint32_t slice_eyes,
+                      uint32_t max_jobs, int rangemin_variant, hrr_server **out) {
+    if (!ctx) return HRR_ERR_INVALID_ARG;
+    if (!out) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_jobs == 0 || max_jobs > 65535)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "max_jobs must be in [1, 65535]");
+    if (rangemin_variant < 0 || rangemin_variant > 2)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2");
+    hrr_server *s = new (std::nothrow) hrr_server();
+    if (!s) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of the server");
+    s->device = ctx->device;
+    s->sm_count = ctx->sm_count;
+    s->variant = rangemin_variant;
+    s->budget = hbm_budget_bytes;
+    s->slice_eyes = slice_eyes ? slice_eyes : (1u << 19);
+    s->max_slots = max_jobs;
+    DeviceGuard g(ctx->device);
+    cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dev_counts, sizeof(unsigned long long) * 2 * max_jobs);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->host_counts, sizeof(unsigned long long) * 2 * max_jobs);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dev_misc, sizeof(unsigned long long) * 2 * kRing);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->host_flags, sizeof(unsigned long long) * kRing);
+    for (int k = 0; k < kRing && e == cudaSuccess; ++k) {
+        e = cudaMalloc(&s->dev_frames[k], sizeof(hrr_cull_frame_t) * max_jobs);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->host_frames[k], sizeof(hrr_cull_frame_t) * max_jobs);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->slice_done[k], cudaEventDisableTiming | cudaEventBlockingSync);
+    }
+    if (e != cudaSuccess) {
+        destroy_resources(s);
+        return hrr_cuda_fail(ctx, e, "server allocation");
+    }
+    for (uint32_t i = 0; i < max_jobs; ++i) s->free_slots.push_back((int)(max_jobs - 1 - i));
+    try {
+        s->thread = std::thread(run, s);
+    } catch (...) {
+        destroy_resources(s);
+        return hrr_fail(ctx, HRR_ERR_OOM, "could not start the scheduler thread");
+    }
+    *out = s;
+    return HRR_OK;
+}
+
+int hrr_server_submit(hrr_server *s, hrr_ctx *ctx, const hrr_job *job, uint64_t *ticket) {
+    if (!s || !job || !ticket) return HRR_ERR_INVALID_ARG;
+    const hrr_job &d = *job;
+    if (!d.tree || d.tree->device != s->device || !(d.tau >= 0.0f) || !(d.tau < __builtin_huge_valf()) ||
+        (d.n_eyes && (!d.eyes.x || !d.eyes.y || !d.eyes.z || !d.eyes.px || !d.eyes.py)))
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job has a NULL or foreign tree, a bad tau or a NULL eye array");
+    const uint32_t *tile = d.dev_tile;
+    uint32_t tw = d.tile_w, th = d.tile_h;
+    if (!tile) {
+        if (!ctx || !ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "job has no tile and no context tile is set");
+        tile = ctx->tile; tw = ctx->tile_w; th = ctx->tile_h;
+    } else if (tw == 0 || th == 0 || tw > 65536 || th > 65536) {
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job tile size is invalid");
+    }
+    Job *j = new (std::nothrow) Job();
+    if (!j) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of a job");
+    j->desc = d;
+    j->tile = tile; j->tile_w = tw; j->tile_h = th;
+    j->bytes = d.cap * sizeof(uint2);
+    j->t_submit = Clock::now();
+    {
+        DeviceGuard g(s->device);
+        if (cudaEventCreateWithFlags(&j->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+            delete j;
+            return hrr_fail(ctx, HRR_ERR_CUDA, "event creation");
+        }
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+        cudaEventDestroy(j->done_ev);
+        delete j;
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "server is shutting down");
+    }
+    j->ticket = s->next_ticket++;
+    s->jobs[j->ticket] = j;
+    if (d.n_eyes == 0) {
+        j->all_launched = true;  // nothing to traverse: completes at once
+        j->status = HRR_OK;
+        j->done = true;
+        j->admitted = true;
+        j->t_admit = j->t_done = j->t_submit;
+        ++s->jobs_done;
+    } else {
+        s->pending.push_back(j);
+    }
+    *ticket = j->ticket;
+    s->cv_work.notify_one();
+    return HRR_OK;
+}
+
+int hrr_server_poll(hrr_server *s, uint64_t ticket, hrr_job_result *res) {
+    if (!s) return HRR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return HRR_ERR_INVALID_ARG;
+    fill_result(it->second, res);
+    return it->second->done ? HRR_OK : HRR_PENDING;
+}
+
+int hrr_server_wait(hrr_server *s, uint64_t ticket, double timeout_s, hrr_job_result *res) {
+    if (!s) return HRR_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) return HRR_ERR_INVALID_ARG;
+    Job *j = it->second;
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0));
+    while (!j->done) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !j->done) {
+            fill_result(j, res);
+            return HRR_ERR_TIMEOUT;
+        }
+    }
+    fill_result(j, res);
+    return HRR_OK;
+}
+
+int hrr_server_release(hrr_server *s, uint64_t ticket) {
+    if (!s) return HRR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end() || !it->second->done) return HRR_ERR_INVALID_ARG;
+    Job *j = it->second;
+    DeviceGuard g(s->device);
+    if (j->pairs) cudaFreeAsync(j->pairs, s->stream);
+    if (j->admitted) s->used -= j->bytes;
+    if (j->done_ev) cudaEventDestroy(j->done_ev);
+    s->jobs.erase(it);
+    delete j;
+    s->cv_work.notify_one();
+    return HRR_OK;
+}
+
+int hrr_server_copy_pairs(hrr_server *s, uint64_t ticket, uint32_t *host_pairs, uint64_t max_pairs,
+                          uint64_t *copied) {
+    if (!s || (!host_pairs && max_pairs)) return HRR_ERR_INVALID_ARG;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end() || !it->second->done) return HRR_ERR_INVALID_ARG;
+    const Job *j = it->second;
+    const uint64_t n = std::min(std::min(j->count, j->desc.cap), max_pairs);
+    if (copied) *copied = 0;
+    if (n && j->pairs) {
+        // The job is done, so its pairs are final; copy them without waiting for the slices
+        // still running on the server stream (the caller must not release this ticket
+        // concurrently).
+        const void *src = j->pairs;
+        lk.unlock();
+        DeviceGuard g(s->device);
+        if (cudaMemcpy(host_pairs, src, n * sizeof(uint2), cudaMemcpyDeviceToHost) != cudaSuccess) return HRR_ERR_CUDA;
+    }
+    if (copied) *copied = n;
+    return HRR_OK;
+}
+
+int hrr_server_stats(hrr_server *s, hrr_server_info *info) {
+    if (!s || !info) return HRR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    info->slices = s->slices;
+    info->launches = s->launches;
+    info->jobs_done = s->jobs_done;
+    info->jobs_waiting = s->pending.size();
+    info->jobs_active = s->active.size();
+    info->max_active = s->max_active;
+    info->bytes_reserved = s->used;
+    return HRR_OK;
+}
+
+int hrr_server_destroy(hrr_server *s) {
+    if (!s) return HRR_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv_work.notify_one();
+    }
+    if (s->thread.joinable()) s->thread.join();
+    DeviceGuard g(s->device);
+    destroy_resources(s);
+    return HRR_OK;
+}
+
+}  // extern "C"

@@ -179,15 +179,20 @@ def shift_tile(w: int, h: int, seed: int) -> np.ndarray:
 # --------------------------------------------------------------------------------------
 
 def calibrate_tau(light_pos: np.ndarray, intensity: np.ndarray, eye_pos: np.ndarray,
-                  target: float) -> np.float32:
+                  target: float, max_lights: int = 0) -> np.float32:
     """tau such that mean_j sum_i min(1, tau*I_i / max(|l_i - e_j|^2, 1e-4)) == target.
 
     Evaluated in float64 over the given eye sample (a workload-shaping step: the exact
     float32 rule that decides acceptance lives in the method, not here). Solved by
-    bisection in log space over sorted per-pair ratios.
+    bisection in log space over sorted per-pair ratios. With max_lights > 0, every k-th
+    light stands for k lights (k = ceil(N_l / max_lights)).
     """
-    lp = light_pos.astype(np.float64)
-    li = intensity.astype(np.float64)
+    stride = 1
+    if max_lights and len(light_pos) > max_lights:
+        stride = -(-len(light_pos) // max_lights)
+    lp = light_pos[::stride].astype(np.float64)
+    li = intensity[::stride].astype(np.float64)
+    target = target / stride
     xs = []
     for e in eye_pos.astype(np.float64):
         d2 = ((lp - e) ** 2).sum(axis=1)
@@ -287,7 +292,7 @@ def gaussian_mixture_lights(n_lights: int, n_comp: int, seed: int,
 def scene_frame(width: int = 1920, height: int = 1080, n_lights: int = 1 << 20,
                 tile_w: int = 64, tile_h: int = 64, target: float = 64.0,
                 n_comp: int = 64, sigma_i: float = 1.5, seed: int = 2,
-                tau_eyes: int = 32) -> Scene:
+                tau_eyes: int = 32, tau_lights: int = 0) -> Scene:
     """Frame-sized workload: eye j at pixel (j mod width, j div width) with position
     (u, v, heightfield(u, v)), u = (px + U)/width, v = (py + U)/height; lights from a
     Gaussian mixture; lognormal(0, sigma_i) intensities; a tile_w x tile_h shift tile;
@@ -301,7 +306,8 @@ def scene_frame(width: int = 1920, height: int = 1080, n_lights: int = 1 << 20,
     light_pos = gaussian_mixture_lights(n_lights, n_comp, seed)
     intensity = np.exp(sigma_i * normal(seed, 21, n_lights)).astype(np.float32)
     tile = shift_tile(tile_w, tile_h, seed)
-    tau = calibrate_tau(light_pos, intensity, eye_pos[_eye_sample(n_e, tau_eyes)], target)
+    tau = calibrate_tau(light_pos, intensity, eye_pos[_eye_sample(n_e, tau_eyes)], target,
+                        max_lights=tau_lights)
     return Scene(name=f"frame_{width}x{height}_{n_lights}", light_pos=light_pos,
                  intensity=intensity, eye_pos=eye_pos, px=px, py=py, tile=tile, tau=tau)
 
@@ -316,3 +322,35 @@ def rangemin_queries(n: int, seed: int = 3):
     b = a + ln
     r = (splitmix64(seed, 32, n) >> np.uint64(32)).astype(np.uint32)
     return a.astype(np.uint32), b.astype(np.uint32), r
+
+
+def log_uniform_int(seed: int, stream: int, n: int, lo: int, hi: int) -> np.ndarray:
+    """n integers log-uniform in [lo, hi]."""
+    u = uniform01(seed, stream, n)
+    return np.floor(np.exp(np.log(lo) + u * (np.log(hi + 1) - np.log(lo)))).astype(np.int64).clip(lo, hi)
+
+
+def frame_sizes(n_frames: int = 64, seed: int = 4, eyes=(65536, 2073600), lights=(16384, 4194304),
+                targets=(16.0, 128.0)):
+    """Per-frame (width, height, n_lights, target) of the batched workload: N_e and N_l
+    log-uniform in the given ranges (eyes laid out as a 16:9 frame of about N_e pixels),
+    target accepted lights per eye uniform in ``targets``."""
+    ne = log_uniform_int(seed, 40, n_frames, *eyes)
+    nl = log_uniform_int(seed, 41, n_frames, *lights)
+    tg = targets[0] + (targets[1] - targets[0]) * uniform01(seed, 42, n_frames)
+    out = []
+    for e, l_, t in zip(ne, nl, tg):
+        w = max(1, int(round(math.sqrt(e * 16.0 / 9.0))))
+        h = max(1, int(round(e / w)))
+        out.append((w, h, int(l_), float(t)))
+    return out
+
+
+def batch_frames(n_frames: int = 64, seed: int = 4, **kw):
+    """The batched workload: frames as in ``scene_frame`` with per-frame seeds, sizes and
+    targets from ``frame_sizes`` (tau calibrated on a light subsample)."""
+    frames = []
+    for f, (w, h, n_l, t) in enumerate(frame_sizes(n_frames, seed, **kw)):
+        frames.append(scene_frame.__wrapped__(width=w, height=h, n_lights=n_l, target=t,
+                                              seed=1000 * seed + f, tau_eyes=16, tau_lights=65536))
+    return frames

@@ -1,0 +1,127 @@
+"""Batched culling through the C ABI: every frame of a batch gets exactly what a plain
+hrr_cull of that frame gets (connection set and per-eye visits), whether the batch runs
+as a recorded CUDA graph or not, on replays, and alongside frames of very different sizes."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import dev, run_cull, sorted_pairs, upload_scene
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_1907_12343_gb300 as hrr
+    c = hrr.Context(0)
+    yield c
+    c.close()
+
+
+def _scenes():
+    s1 = dict(synth.scene_frame(width=257, height=131, n_lights=50021, tile_w=64, tile_h=64,
+                                target=64.0, seed=7))
+    s2 = dict(synth.scene_uniform())
+    s3 = dict(synth.scene_frame(width=61, height=37, n_lights=5003, tile_w=16, tile_h=16,
+                                target=48.0, seed=5))
+    one = dict(synth.scene_uniform(n_lights=64, grid_w=16, grid_h=8, tile_w=8, tile_h=8,
+                                   target=4.0, seed=9))
+    one["light_pos"], one["intensity"] = one["light_pos"][:1], one["intensity"][:1]
+    one["tau"] = np.float32(one["tau"] * 20)
+    empty = dict(synth.scene_uniform(n_lights=300, grid_w=8, grid_h=4, tile_w=8, tile_h=8, seed=10))
+    empty["eye_pos"], empty["px"], empty["py"] = empty["eye_pos"][:0], empty["px"][:0], empty["py"][:0]
+    return [s1, s2, s3, one, empty]
+
+
+def _frame(ctx, s, cap, shift_offset=0):
+    import torch
+    g = upload_scene(s)
+    tree = ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"])
+    n = g["ex"].numel()
+    tile = torch.from_numpy(np.ascontiguousarray(s["tile"]).view(np.int32)).to(dev())
+    return {"x": g["ex"], "y": g["ey"], "z": g["ez"], "px": g["px"], "py": g["py"], "tree": tree,
+            "tau": float(s["tau"]), "tile": tile, "shift_offset": shift_offset,
+            "pairs": torch.empty((cap, 2), dtype=torch.int32, device=dev()),
+            "eye_visits": torch.zeros(max(n, 1), dtype=torch.int32, device=dev()), "_g": g, "_s": s}
+
+
+def _plain(ctx, fr):
+    ctx.set_shift_tile(fr["_s"]["tile"])
+    n = fr["x"].numel()
+    st, cnt, pairs, vis = run_cull(ctx, fr["_g"], fr["tree"], fr["tau"], visits=n > 0,
+                                   shift_offset=fr["shift_offset"])
+    return st, pairs, vis
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_plain_per_frame(ctx, use_graph):
+    import paper_1907_12343_gb300 as hrr
+    frames = [_frame(ctx, s, cap=max(1024, 256 * len(s["eye_pos"])), shift_offset=o)
+              for s, o in zip(_scenes(), [0, 0x9E3779B9, 0, 7, 0])]
+    b = hrr.Batch(ctx, frames, use_graph=use_graph)
+    for rep in range(2):  # a replay must reset the counters
+        b.launch()
+        st, counts, visits = b.results()
+        assert st == hrr.HRR_OK
+        for fr, cnt, v in zip(frames, counts, visits):
+            n = fr["x"].numel()
+            got = fr["pairs"][:cnt].cpu().numpy().view(np.uint32)
+            if rep == 1:
+                continue
+            pst, ref, ref_vis = _plain(ctx, fr)
+            assert pst == hrr.HRR_OK
+            assert np.array_equal(sorted_pairs(got), sorted_pairs(ref))
+            if n:
+                ev = fr["eye_visits"][:n].cpu().numpy().view(np.uint32)
+                assert np.array_equal(ev, ref_vis)
+                assert v == int(ref_vis.sum())
+            else:
+                assert cnt == 0 and v == 0
+    # the first (uniform) scene also against the flat oracle
+    s = frames[1]["_s"]
+    t = oracle.Tree(s["light_pos"], s["intensity"])
+    tile = (s["tile"].astype(np.uint64) + 0x9E3779B9).astype(np.uint32)
+    flat = oracle.cull_flat(t, s["eye_pos"], s["px"], s["py"], tile, s["tau"])
+    got = frames[1]["pairs"][:counts[1]].cpu().numpy().view(np.uint32)
+    assert np.array_equal(sorted_pairs(got), sorted_pairs(flat["pairs"]))
+    b.destroy()
+    for fr in frames:
+        fr["tree"].free()
+
+
+def test_batch_overflow_is_per_frame(ctx):
+    import paper_1907_12343_gb300 as hrr
+    scenes = _scenes()[:3]
+    frames = [_frame(ctx, s, cap=max(1024, 256 * len(s["eye_pos"]))) for s in scenes]
+    frames[1]["pairs"] = frames[1]["pairs"][:100]
+    b = hrr.Batch(ctx, frames, use_graph=True)
+    b.launch()
+    st, counts, _ = b.results()
+    assert st == hrr.HRR_ERR_OVERFLOW
+    assert counts[1] > 100
+    st0, ref0, _ = _plain(ctx, frames[0])
+    assert np.array_equal(sorted_pairs(frames[0]["pairs"][:counts[0]].cpu().numpy().view(np.uint32)),
+                          sorted_pairs(ref0))
+    b.destroy()
+    for fr in frames:
+        fr["tree"].free()
+
+
+def test_batch_validation(ctx):
+    import paper_1907_12343_gb300 as hrr
+    c = hrr.Context(0)  # no context tile
+    s = _scenes()[1]
+    fr = _frame(c, s, cap=4096)
+    fr_no_tile = dict(fr)
+    fr_no_tile["tile"] = None
+    with pytest.raises(hrr.HRRError) as e:
+        hrr.Batch(c, [fr_no_tile])
+    assert e.value.status == hrr.HRR_ERR_NO_TILE
+    bad = dict(fr)
+    bad["tau"] = float("nan")
+    with pytest.raises(hrr.HRRError) as e:
+        hrr.Batch(c, [fr, bad])
+    assert e.value.status == hrr.HRR_ERR_INVALID_ARG
+    fr["tree"].free()
+    c.close()
