@@ -194,13 +194,7 @@ def run_ours(args):
     ctx.set_timing(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_rank = sum(step_ms) / len(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([t_rank], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
-    else:
-        t_step = t_rank
-    value = ws * n_e * n_l / t_step
+    value, t_step = aggregate_throughput(n_e * n_l, t_rank, dist, dev)
 
     # cull-only throughput and the traversal kernel's roofline figures
     cull_ms = kern_ms / max(kern_n, 1)
@@ -295,6 +289,21 @@ def profiled_traffic():
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def aggregate_throughput(units_per_rank: float, t_rank: float, dist=None, device="cpu"):
+    """Whole-job throughput of a weak-scaled run: every rank processes units_per_rank in
+    t_rank seconds; the job takes the slowest rank's time (the only collective of the
+    benchmark, a max-reduction of one number). Returns (units/s over all ranks, max time)."""
+    import torch
+    ws = 1
+    t = t_rank
+    if dist is not None and dist.is_initialized():
+        ws = dist.get_world_size()
+        x = torch.tensor([t_rank], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return ws * units_per_rank / t, t
 
 
 def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk):

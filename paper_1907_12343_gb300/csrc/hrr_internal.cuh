@@ -336,14 +336,3 @@ __device__ __forceinline__ bool hrr_node_culls(uint32_t v, float den, float rhs)
     const float w = __fmul_rn(__uint2float_rd(v), 2.3283064365386963e-10f);  // exact * 2^-32
     return __fmul_rd(w, den) >= rhs;
 }
-
-// Could any range of length L >= 1 be culled? Its minimum is below 2^(33 - fls(L)): the
-// values brev(i) of 2^h consecutive indices fall one into each dyadic interval of width
-// 2^(32-h), so the interval after the one holding 1 - r (cyclically) holds a value less
-// than 2^(33-h) above it. If even that bound cannot cull, the range minimum is not needed.
-__device__ __forceinline__ bool hrr_node_may_cull(uint32_t L, float den, float rhs) {
-    if (!(rhs < __int_as_float(0x7f800000))) return false;
-    const int h = 31 - __clz(L);
-    const float wmax = __int_as_float((128 - h) << 23);  // 2^(1 - h)
-    return __fmul_rd(wmax, den) >= rhs;
-}
