@@ -214,11 +214,12 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             batched = run_batched(ctx, frames, stream, dev)
             if args.served_jobs > 0:
-                served = {"config": run_served(ctx, frames, stream, dev, args.served_jobs, 200.0)}
+                tn = {k: batched["tuning"][k] for k in ("rangemin_variant", "blocks_per_sm", "refill_below")}
+                served = {"config": run_served(ctx, frames, stream, dev, args.served_jobs, 200.0, tuning=tn)}
                 # the same at a load the GPU can sustain: 70% of its job-by-job capacity
                 cap_jobs = args.batch_frames / (batched["plain_job_by_job"]["ms"] / 1e3)
                 served["sustainable"] = run_served(ctx, frames, stream, dev, max(16, args.served_jobs // 4),
-                                                   0.7 * cap_jobs, seed=12)
+                                                   0.7 * cap_jobs, seed=12, tuning=tn)
         for fr in frames:
             fr["tree"].free()
 
@@ -400,14 +401,15 @@ def upload_frames(ctx, frames_np, dev):
     return out
 
 
-def plain_frame(ctx, fr, pairs, stream):
+def plain_frame(ctx, fr, pairs, stream, tuning=None):
     """One frame through hrr_cull on the context stream: (ms on the device, count)."""
     import torch
     import paper_1907_12343_gb300 as hrr
     ctx.set_shift_tile(fr["tile_np"])
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    st, cnt = ctx.cull(fr["x"], fr["y"], fr["z"], fr["px"], fr["py"], fr["tree"], fr["tau"], pairs)
+    st, cnt = ctx.cull(fr["x"], fr["y"], fr["z"], fr["px"], fr["py"], fr["tree"], fr["tau"], pairs,
+                       tuning=tuning)
     b.record(stream)
     b.synchronize()
     if st != hrr.HRR_OK:
@@ -421,17 +423,32 @@ def run_batched(ctx, frames, stream, dev, runs=3):
     import torch
     import paper_1907_12343_gb300 as hrr
     total_pairs = sum(fr["n_e"] * fr["n_l"] for fr in frames)
+    # One launch takes one tuning: that of the size class holding the most eyes, tuned on
+    # a sample of its largest frame (the launch time follows the eye count).
+    from paper_1907_12343_gb300.autotune import Autotuner, size_class
+    by_class = {}
+    for fr in frames:
+        by_class.setdefault(size_class(fr["n_e"], fr["n_l"]), []).append(fr)
+    cls, members = max(by_class.items(), key=lambda kv: sum(fr["n_e"] for fr in kv[1]))
+    big = max(members, key=lambda fr: fr["n_e"])
+    tuner = Autotuner(ctx)
+    t_tune = time.perf_counter()
+    ctx.set_shift_tile(big["tile_np"])
+    entry = tuner.tune(big["x"], big["y"], big["z"], big["px"], big["py"], big["tree"], big["tau"],
+                       n_lights=big["n_l"])
+    t_tune = time.perf_counter() - t_tune
+    tuning = Autotuner.launch_fields(entry)
     scratch = torch.empty((max(fr["n_e"] for fr in frames) * 200, 2), dtype=torch.int32, device=dev)
     plain_ms, counts = [], []
     for fr in frames:
-        ms, cnt = plain_frame(ctx, fr, scratch, stream)
+        ms, cnt = plain_frame(ctx, fr, scratch, stream, tuning)
         plain_ms.append(ms)
         counts.append(cnt)
     del scratch
     for fr, cnt in zip(frames, counts):
         fr["count"] = cnt
         fr["pairs"] = torch.empty((cnt + 1024, 2), dtype=torch.int32, device=dev)
-    b = hrr.Batch(ctx, frames, use_graph=True)
+    b = hrr.Batch(ctx, frames, use_graph=True, tuning=tuning)
     b.launch()
     st, got, _ = b.results()
     if st != hrr.HRR_OK or got != counts:
@@ -452,7 +469,9 @@ def run_batched(ctx, frames, stream, dev, runs=3):
             "lights": sum(fr["n_l"] for fr in frames), "accepted_pairs": int(sum(counts)),
             "value": total_pairs / t_b, "unit": UNIT, "ms": t_b * 1e3, "graph": True,
             "plain_job_by_job": {"value": total_pairs / t_p, "ms": t_p * 1e3},
-            "speedup_vs_plain": t_p / t_b}
+            "speedup_vs_plain": t_p / t_b,
+            "tuning": dict(tuning, size_class=cls, sample_eyes=min(big["n_e"], tuner.sample),
+                           sample_ms=entry["sample_ms"], tune_s=t_tune)}
 
 
 def _latency_stats(lat):
@@ -462,7 +481,8 @@ def _latency_stats(lat):
             "max_s": float(a[-1])}
 
 
-def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30):
+def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30, slice_eyes=1 << 20,
+               tuning=None):
     """Poisson arrivals of frame-sized jobs against resident hierarchies and tiles, served
     with continuous batching, against the same arrival sequence processed job by job."""
     import threading as th
@@ -476,7 +496,7 @@ def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30
     work = sum(frames[f]["n_e"] * frames[f]["n_l"] for f in which)
 
     # served
-    srv = hrr.Server(ctx, budget, slice_eyes=1 << 19, max_jobs=max(64, n_jobs))
+    srv = hrr.Server(ctx, budget, slice_eyes=slice_eyes, max_jobs=max(64, n_jobs), tuning=tuning)
     tickets = [None] * n_jobs
     t0 = time.perf_counter()
 
@@ -513,10 +533,10 @@ def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30
         dt = t0 + arrive[k] - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
-        plain_frame(ctx, frames[which[k]], scratch, stream)
+        plain_frame(ctx, frames[which[k]], scratch, stream, tuning)
         lat_p.append(time.perf_counter() - t0 - arrive[k])
     makespan_p = time.perf_counter() - t0
-    return {"jobs": n_jobs, "rate_per_s": rate, "hbm_budget_gb": budget / 2**30,
+    return {"jobs": n_jobs, "rate_per_s": rate, "hbm_budget_gb": budget / 2**30, "slice_eyes": slice_eyes,
             "value": work / makespan, "unit": UNIT, "latency": _latency_stats(lat),
             "max_active": stats["max_active"], "slices": stats["slices"], "mismatched_jobs": mismatch,
             "plain_job_by_job": {"value": work / makespan_p, "latency": _latency_stats(lat_p)}}

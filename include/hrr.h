@@ -107,7 +107,19 @@ typedef struct hrr_cull_opts {
     /* added (mod 2^32) to every eye's shift: the sample offset psi(n) of the adaptive
      * sampling variant (Sec. 3), absorbed into the shift; 0 for the plain method */
     uint32_t shift_offset;
+    /* launch shape (results do not depend on it): resident blocks per SM of the persistent
+     * grid (0 = as many as fit), and the number of busy lanes below which a warp refills
+     * its idle lanes with new eyes (1..32, 0 = 29); see hrr_autotune */
+    uint32_t blocks_per_sm;
+    uint32_t refill_below;
 } hrr_cull_opts;
+
+/* Launch parameters of the traversal (see hrr_cull_opts); none changes any result. */
+typedef struct hrr_tuning {
+    int rangemin_variant;
+    uint32_t blocks_per_sm;
+    uint32_t refill_below;
+} hrr_tuning;
 
 /* ---- context --------------------------------------------------------------------------- */
 
@@ -226,10 +238,11 @@ typedef struct hrr_batch hrr_batch; /* opaque, library-owned */
 /* Prepare a batch of 1..65535 frames for repeated culling: validates the frames, uploads
  * their descriptors and per-frame counters to the device and, when use_graph != 0, records
  * the launch (counter reset + one persistent traversal over every frame's eyes) into a
- * CUDA graph. The frames' memory must stay valid while the batch exists. Synchronous.
+ * CUDA graph. tuning may be NULL (defaults). The frames' memory must stay valid while the
+ * batch exists. Synchronous.
  * Status HRR_ERR_NO_TILE if a frame has no tile and the context has none. */
 int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames,
-                     int rangemin_variant, int use_graph, hrr_batch **out);
+                     const hrr_tuning *tuning, int use_graph, hrr_batch **out);
 /* Enqueue one run of the batch on the context stream (a graph replay when recorded).
  * Asynchronous. */
 int hrr_batch_launch(hrr_ctx *ctx, hrr_batch *batch);
@@ -241,7 +254,7 @@ int hrr_batch_results(hrr_ctx *ctx, hrr_batch *batch, uint64_t *counts, uint64_t
 int hrr_batch_destroy(hrr_ctx *ctx, hrr_batch *batch);
 /* One-shot batch: create (no graph), launch, results, destroy. */
 int hrr_cull_batch(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames,
-                   int rangemin_variant, uint64_t *counts);
+                   const hrr_tuning *tuning, uint64_t *counts);
 
 /* ---- served culling (continuous batching) --------------------------------------------- */
 
@@ -281,13 +294,14 @@ typedef struct hrr_server hrr_server; /* opaque, library-owned */
 /* Start a server on ctx's device with its own stream and scheduler thread. Jobs are
  * admitted in arrival order while their output reservations (cap * 8 bytes) fit in
  * hbm_budget_bytes and fewer than max_jobs are admitted; the GPU then runs slices, each
- * one batched traversal over up to slice_eyes (0: 2^19) of the admitted jobs' remaining
+ * one batched traversal over up to slice_eyes (0: 2^20) of the admitted jobs' remaining
  * eyes, oldest job first, so jobs arriving while others run join a slice as soon as the
  * older jobs leave room. Each job's result is exactly what hrr_cull would produce for it
- * alone. The server never makes the GPU wait on the host. rangemin_variant as in
- * hrr_cull_opts. */
+ * alone. Slices alternate between two streams so that each one's tail overlaps the next.
+ * Job outputs come from a memory pool of the server that keeps freed memory up to the
+ * budget. The server never makes the GPU wait on the host. tuning may be NULL (defaults). */
 int hrr_server_create(hrr_ctx *ctx, uint64_t hbm_budget_bytes, uint32_t slice_eyes,
-                      uint32_t max_jobs, int rangemin_variant, hrr_server **out);
+                      uint32_t max_jobs, const hrr_tuning *tuning, hrr_server **out);
 /* Queue a job (thread-safe, non-blocking); *ticket identifies it. ctx (may be NULL when the
  * job has its own tile) receives the error text of a rejected job. */
 int hrr_server_submit(hrr_server *server, hrr_ctx *ctx, const hrr_job *job, uint64_t *ticket);
@@ -305,6 +319,16 @@ int hrr_server_release(hrr_server *server, uint64_t ticket);
 int hrr_server_stats(hrr_server *server, hrr_server_info *info);
 /* Finish every submitted job, stop the scheduler and free everything the server owns. */
 int hrr_server_destroy(hrr_server *server);
+
+/* ---- autotuning ---------------------------------------------------------------------- */
+
+/* Time every candidate launch shape (range-minimum variants 0 and 2, 2..4 blocks per SM,
+ * refill thresholds 24 / 29 / 32) on the given eyes (a sample of a workload's size class)
+ * and return the fastest in *best (its median time in *best_ms, may be NULL). dev_pairs /
+ * cap as in hrr_cull and large enough for the sample. Results of every candidate are
+ * identical; only the time differs. Synchronous. */
+int hrr_autotune(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
+                 uint32_t *dev_pairs, uint64_t cap, hrr_tuning *best, double *best_ms);
 
 /* ---- range minimum (Sec. 2, Alg. 1-3) -------------------------------------------------- */
 

@@ -84,7 +84,24 @@ class hrr_server_info(C.Structure):
 
 class hrr_cull_opts(C.Structure):
     _fields_ = [("eye_visits", C.c_void_p), ("rangemin_variant", C.c_int),
-                ("shift_offset", C.c_uint32)]
+                ("shift_offset", C.c_uint32), ("blocks_per_sm", C.c_uint32),
+                ("refill_below", C.c_uint32)]
+
+
+class hrr_tuning(C.Structure):
+    _fields_ = [("rangemin_variant", C.c_int), ("blocks_per_sm", C.c_uint32),
+                ("refill_below", C.c_uint32)]
+
+    @classmethod
+    def from_dict(cls, d):
+        if d is None:
+            return None
+        return cls(int(d.get("rangemin_variant", 0)), int(d.get("blocks_per_sm", 0)),
+                   int(d.get("refill_below", 0)))
+
+    def to_dict(self):
+        return {"rangemin_variant": int(self.rangemin_variant), "blocks_per_sm": int(self.blocks_per_sm),
+                "refill_below": int(self.refill_below)}
 
 
 _P = C.c_void_p
@@ -110,12 +127,14 @@ _SIGS = {
     "hrr_range_min": (_i32, [_P, _P, _P, _P, _P, _P, _u64, _i32]),
     "hrr_build_light_tree_static": (_i32, [hrr_lights, _u32, _P, _P, C.POINTER(_u32), _P,
                                            C.c_char_p, C.c_size_t]),
-    "hrr_batch_create": (_i32, [_P, C.POINTER(hrr_frame), _u32, _i32, _i32, C.POINTER(_P)]),
+    "hrr_batch_create": (_i32, [_P, C.POINTER(hrr_frame), _u32, C.POINTER(hrr_tuning), _i32, C.POINTER(_P)]),
     "hrr_batch_launch": (_i32, [_P, _P]),
     "hrr_batch_results": (_i32, [_P, _P, C.POINTER(_u64), C.POINTER(_u64)]),
     "hrr_batch_destroy": (_i32, [_P, _P]),
-    "hrr_cull_batch": (_i32, [_P, C.POINTER(hrr_frame), _u32, _i32, C.POINTER(_u64)]),
-    "hrr_server_create": (_i32, [_P, _u64, _u32, _u32, _i32, C.POINTER(_P)]),
+    "hrr_cull_batch": (_i32, [_P, C.POINTER(hrr_frame), _u32, C.POINTER(hrr_tuning), C.POINTER(_u64)]),
+    "hrr_server_create": (_i32, [_P, _u64, _u32, _u32, C.POINTER(hrr_tuning), C.POINTER(_P)]),
+    "hrr_autotune": (_i32, [_P, hrr_eyes, _u32, _P, _f32, _P, _u64, C.POINTER(hrr_tuning),
+                            C.POINTER(C.c_double)]),
     "hrr_server_submit": (_i32, [_P, _P, C.POINTER(hrr_job), C.POINTER(_u64)]),
     "hrr_server_poll": (_i32, [_P, _u64, C.POINTER(hrr_job_result)]),
     "hrr_server_wait": (_i32, [_P, _u64, C.c_double, C.POINTER(hrr_job_result)]),
@@ -196,14 +215,17 @@ class Context:
 
     # -- culling ---------------------------------------------------------------------------
     def cull(self, x, y, z, px, py, tree: "Tree", tau: float, pairs, eye_visits=None,
-             rangemin_variant: int = 0, shift_offset: int = 0):
+             rangemin_variant: int = 0, shift_offset: int = 0, tuning=None):
         """Cull into ``pairs`` (uint32/int32 tensor of shape (cap, 2)); returns
-        (status, count). HRR_ERR_OVERFLOW is returned, not raised."""
+        (status, count). HRR_ERR_OVERFLOW is returned, not raised. ``tuning`` (a dict as
+        returned by autotune) sets the launch shape and overrides rangemin_variant."""
         n = int(x.numel())
         E = hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py))
         cap = int(pairs.shape[0]) if pairs is not None else 0
         cnt = _u64()
-        opts = hrr_cull_opts(_ptr(eye_visits), rangemin_variant, shift_offset)
+        t = tuning or {}
+        opts = hrr_cull_opts(_ptr(eye_visits), int(t.get("rangemin_variant", rangemin_variant)),
+                             shift_offset, int(t.get("blocks_per_sm", 0)), int(t.get("refill_below", 0)))
         st = hrr_cull_ex(self.handle, E, n, tree.handle, float(tau), C.byref(opts),
                          _ptr(pairs) if cap else None, cap, C.byref(cnt))
         if st not in (HRR_OK, HRR_ERR_OVERFLOW):
@@ -214,6 +236,15 @@ class Context:
         v, a = _u64(), _u64()
         self.check(hrr_last_cull_stats(self.handle, C.byref(v), C.byref(a)))
         return int(v.value), int(a.value)
+
+    def autotune(self, x, y, z, px, py, tree: "Tree", tau: float, pairs):
+        """Fastest launch shape on these eyes: (tuning dict, median ms)."""
+        E = hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py))
+        best = hrr_tuning()
+        ms = C.c_double()
+        self.check(hrr_autotune(self.handle, E, int(x.numel()), tree.handle, float(tau), _ptr(pairs),
+                                int(pairs.shape[0]), C.byref(best), C.byref(ms)))
+        return best.to_dict(), float(ms.value)
 
     def range_min(self, a, b, r, out_min, out_argmin=None, variant: int = 0):
         self.check(hrr_range_min(self.handle, _ptr(a), _ptr(b), _ptr(r), _ptr(out_min),
@@ -241,7 +272,8 @@ class Batch:
     eyes), tree (Tree), tau, pairs (int32 tensor (cap, 2)); optional tile (uint32 tensor
     (h, w) on the device), shift_offset, eye_visits (int32 tensor)."""
 
-    def __init__(self, ctx: "Context", frames, rangemin_variant: int = 0, use_graph: bool = True):
+    def __init__(self, ctx: "Context", frames, rangemin_variant: int = 0, use_graph: bool = True,
+                 tuning=None):
         self.ctx = ctx
         self.n = len(frames)
         arr = (hrr_frame * self.n)()
@@ -257,7 +289,8 @@ class Batch:
                 _ptr(fr["pairs"]) if fr["pairs"].shape[0] else None, int(fr["pairs"].shape[0]),
                 _ptr(fr.get("eye_visits")))
         h = _P()
-        ctx.check(hrr_batch_create(ctx.handle, arr, self.n, rangemin_variant, 1 if use_graph else 0,
+        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0, 0)
+        ctx.check(hrr_batch_create(ctx.handle, arr, self.n, C.byref(tn), 1 if use_graph else 0,
                                    C.byref(h)))
         self.handle = h
 
@@ -293,11 +326,12 @@ class Server:
     wait()/poll() give the result, release() frees the job's output buffer."""
 
     def __init__(self, ctx: "Context", hbm_budget_bytes: int, slice_eyes: int = 0,
-                 max_jobs: int = 1024, rangemin_variant: int = 0):
+                 max_jobs: int = 1024, rangemin_variant: int = 0, tuning=None):
         self.ctx = ctx
         h = _P()
+        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0, 0)
         ctx.check(hrr_server_create(ctx.handle, int(hbm_budget_bytes), int(slice_eyes), int(max_jobs),
-                                    rangemin_variant, C.byref(h)))
+                                    C.byref(tn), C.byref(h)))
         self.handle = h
         self._keep = {}
 

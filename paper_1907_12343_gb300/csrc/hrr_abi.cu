@@ -225,8 +225,8 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
     if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
     hrr_cull_opts o{};
     if (opts) o = *opts;
-    if (o.rangemin_variant < 0 || o.rangemin_variant > 2)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2");
+    if (o.rangemin_variant < 0 || o.rangemin_variant > 2 || o.refill_below > 32)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2 and refill_below <= 32");
     DeviceGuard g(ctx->device);
     return hrr_cull_impl(ctx, eyes, n_eyes, tree, tau, o, dev_pairs, cap, out_count);
 }

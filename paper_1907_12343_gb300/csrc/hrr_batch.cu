@@ -13,7 +13,7 @@
 struct hrr_batch {
     uint32_t n_frames = 0;
     unsigned long long total = 0;
-    int variant = 0;
+    hrr_tuning tuning{};
     hrr_cull_frame_t *dev_frames = nullptr;
     unsigned long long *dev_counts = nullptr;  // 2 per frame (accepted, visits), then cursor, flags
     unsigned long long *host_counts = nullptr; // pinned mirror
@@ -29,7 +29,7 @@ int enqueue(hrr_ctx *ctx, hrr_batch *b, cudaStream_t st) {
     HRR_CUDA(ctx, cudaMemsetAsync(b->dev_counts, 0, bytes, st));
     unsigned long long *misc = b->dev_counts + 2 * (size_t)b->n_frames;
     HRR_CUDA(ctx, hrr_cull_batch_enqueue(ctx->sm_count, b->dev_frames, b->n_frames, b->total, misc,
-                                         misc + 1, b->variant, st));
+                                         misc + 1, b->tuning, st));
     if (b->total) ++ctx->launches;
     return HRR_OK;
 }
@@ -47,20 +47,20 @@ void release(hrr_batch *b) {
 
 extern "C" {
 
-int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, int rangemin_variant,
+int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, const hrr_tuning *tuning,
                      int use_graph, hrr_batch **out) {
     if (!ctx) return HRR_ERR_INVALID_ARG;
     if (!out) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!frames || n_frames == 0 || n_frames > 65535)
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "n_frames must be in [1, 65535]");
-    if (rangemin_variant < 0 || rangemin_variant > 2)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2");
+    const hrr_tuning tn = tuning ? *tuning : hrr_tuning{};
+    if (!hrr_tuning_valid(tn)) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "invalid tuning");
     std::vector<hrr_cull_frame_t> desc(n_frames);
     hrr_batch *b = new (std::nothrow) hrr_batch();
     if (!b) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of the batch");
     b->n_frames = n_frames;
-    b->variant = rangemin_variant;
+    b->tuning = hrr_tuning_normalized(tn);
     b->caps.resize(n_frames);
     DeviceGuard g(ctx->device);
     unsigned long long cursor = 0;
@@ -185,10 +185,10 @@ int hrr_batch_destroy(hrr_ctx *ctx, hrr_batch *b) {
     return HRR_OK;
 }
 
-int hrr_cull_batch(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, int rangemin_variant,
+int hrr_cull_batch(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, const hrr_tuning *tuning,
                    uint64_t *counts) {
     hrr_batch *b = nullptr;
-    int st = hrr_batch_create(ctx, frames, n_frames, rangemin_variant, 0, &b);
+    int st = hrr_batch_create(ctx, frames, n_frames, tuning, 0, &b);
     if (st != HRR_OK) return st;
     st = hrr_batch_launch(ctx, b);
     if (st == HRR_OK) st = hrr_batch_results(ctx, b, counts, nullptr);

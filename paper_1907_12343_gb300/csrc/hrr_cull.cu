@@ -30,9 +30,6 @@ namespace {
 #ifndef HRR_CULL_MIN_BLOCKS
 #define HRR_CULL_MIN_BLOCKS 4  // resident 256-thread blocks per SM (64 registers: no spills, best measured)
 #endif
-#ifndef HRR_CULL_REFILL_BELOW
-#define HRR_CULL_REFILL_BELOW 29  // refill a warp's idle lanes once at least 4 are idle
-#endif
 #ifndef HRR_CULL_SMEM_LEVELS
 #define HRR_CULL_SMEM_LEVELS 12  // traversal-stack levels kept in shared memory per thread
 #endif
@@ -48,7 +45,6 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kBuf = HRR_CULL_BUF;
 constexpr int kSmemLevels = HRR_CULL_SMEM_LEVELS;
 constexpr int kStack = 96;       // >= height of any radix tree over 95-bit ordering keys
-constexpr int kRefillBelow = HRR_CULL_REFILL_BELOW;
 constexpr uint32_t kSmemFrames = 64;  // batch frames whose descriptors are staged in shared memory
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
@@ -58,6 +54,7 @@ static_assert(sizeof(Frame) == 128, "frame descriptor layout");
 struct Launch {
     const Frame *frames;            // batch: device array of n_frames descriptors
     uint32_t n_frames;
+    uint32_t refill_below;          // refill a warp's idle lanes once fewer lanes are busy
     unsigned long long total;       // eyes of this launch over all frames
     unsigned long long *cursor;     // global eye cursor (starts at 0)
     unsigned long long *flags;      // HRR_FLAG_* bits
@@ -192,7 +189,7 @@ cull_kernel(const Launch Lc, const Frame single) {
     for (;;) {
         uint32_t acc0 = kNone, acc1 = kNone;
         unsigned alive_mask = __ballot_sync(0xFFFFFFFFu, alive);
-        if (more && __popc(alive_mask) < kRefillBelow) {
+        if (more && (uint32_t)__popc(alive_mask) < Lc.refill_below) {
             const unsigned idle = ~alive_mask;
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(Lc.cursor, (unsigned long long)__popc(idle));
@@ -344,10 +341,12 @@ int blocks_per_sm() {
 }
 
 template <bool BATCH>
-cudaError_t launch_variant(int variant, int sm_count, unsigned long long total, const Launch &Lc,
+cudaError_t launch_variant(const hrr_tuning &tn, int sm_count, unsigned long long total, const Launch &Lc,
                            const Frame &single, cudaStream_t st) {
+    const int variant = tn.rangemin_variant;
     const unsigned long long blocks_needed = (total + kThreads - 1) / kThreads;
     auto grid = [&](int per_sm) {
+        if (tn.blocks_per_sm > 0 && (int)tn.blocks_per_sm < per_sm) per_sm = (int)tn.blocks_per_sm;
         return (unsigned)min((unsigned long long)per_sm * sm_count, blocks_needed);
     };
     if (variant == 0)
@@ -383,9 +382,10 @@ int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tr
         fr.tau = tau;
         fr.eye_begin = 0;
         fr.cursor_begin = 0;
-        const Launch Lc{nullptr, 1, n_eyes, ctx->counters + 3, ctx->counters + 2};
+        const hrr_tuning tn = hrr_tuning_of(opts);
+        const Launch Lc{nullptr, 1, tn.refill_below, n_eyes, ctx->counters + 3, ctx->counters + 2};
         hrr_timing_begin(ctx);
-        const cudaError_t e = launch_variant<false>(opts.rangemin_variant, ctx->sm_count, n_eyes, Lc, fr, st);
+        const cudaError_t e = launch_variant<false>(tn, ctx->sm_count, n_eyes, Lc, fr, st);
         hrr_timing_end(ctx);
         ++ctx->launches;
         HRR_CUDA(ctx, e);
@@ -407,9 +407,10 @@ int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tr
 
 cudaError_t hrr_cull_batch_enqueue(int sm_count, const hrr_cull_frame_t *dev_frames, uint32_t n_frames,
                                    unsigned long long total, unsigned long long *cursor,
-                                   unsigned long long *flags, int variant, cudaStream_t st) {
-    const Launch Lc{dev_frames, n_frames, total, cursor, flags};
+                                   unsigned long long *flags, const hrr_tuning &tuning, cudaStream_t st) {
+    const hrr_tuning tn = hrr_tuning_normalized(tuning);
+    const Launch Lc{dev_frames, n_frames, tn.refill_below, total, cursor, flags};
     const Frame unused{};
     if (total == 0) return cudaSuccess;
-    return launch_variant<true>(variant, sm_count, total, Lc, unused, st);
+    return launch_variant<true>(tn, sm_count, total, Lc, unused, st);
 }

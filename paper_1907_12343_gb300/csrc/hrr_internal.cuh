@@ -84,11 +84,27 @@ struct hrr_cull_frame_t {
     unsigned long long cursor_begin; // where the frame's eyes start on the launch's cursor
 };
 
+// Launch parameters with the library defaults filled in (refill_below 0 -> 29).
+inline hrr_tuning hrr_tuning_normalized(hrr_tuning t) {
+    if (t.refill_below == 0 || t.refill_below > 32) t.refill_below = 29;
+    return t;
+}
+inline hrr_tuning hrr_tuning_of(const hrr_cull_opts &o) {
+    hrr_tuning t{};
+    t.rangemin_variant = o.rangemin_variant;
+    t.blocks_per_sm = o.blocks_per_sm;
+    t.refill_below = o.refill_below;
+    return hrr_tuning_normalized(t);
+}
+inline bool hrr_tuning_valid(const hrr_tuning &t) {
+    return t.rangemin_variant >= 0 && t.rangemin_variant <= 2 && t.refill_below <= 32;
+}
+
 // Enqueue one batched traversal on st (hrr_cull.cu); a no-op when total == 0. The cursor
 // must be zero when the kernel starts. sm_count sizes the persistent grid.
 cudaError_t hrr_cull_batch_enqueue(int sm_count, const hrr_cull_frame_t *dev_frames, uint32_t n_frames,
                                    unsigned long long total, unsigned long long *cursor,
-                                   unsigned long long *flags, int variant, cudaStream_t st);
+                                   unsigned long long *flags, const hrr_tuning &tuning, cudaStream_t st);
 
 // Traversal timing (hrr_abi.cu)
 void hrr_timing_begin(hrr_ctx *ctx);

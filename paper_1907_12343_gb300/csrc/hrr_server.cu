@@ -8,7 +8,9 @@
 //     over up to slice_eyes of the admitted jobs' remaining eyes, oldest job first, so a
 //     job that arrives while others are on the GPU joins a slice as soon as the older jobs
 //     leave room, and its work overlaps theirs;
-//   * keeps at most kRing slices enqueued, so admission reacts within about one slice;
+//   * alternates slices between two streams, so the next slice's blocks fill the SMs as
+//     the previous slice drains (no per-slice tail), and keeps at most kRing slices
+//     enqueued, so admission reacts within about one slice;
 //   * completes a job when the slice holding its last eyes finishes, publishing its pair
 //     count and node visits.
 // The device never waits on the host: all scheduling happens between launches, so no
@@ -53,8 +55,12 @@ struct Job {
 }  // namespace
 
 struct hrr_server {
-    int device = 0, sm_count = 0, variant = 0;
-    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 0;
+    hrr_tuning tuning{};
+    cudaStream_t stream = nullptr;              // slice stream 0 (also for frees)
+    cudaStream_t slice_stream[kRing] = {};      // slice k runs on slice_stream[k]
+    cudaMemPool_t pool = nullptr;               // job outputs; keeps freed memory for reuse
+    int last_slice = -1;                        // ring entry of the most recent slice
     uint64_t budget = 0, used = 0;
     uint32_t slice_eyes = 0, max_slots = 0;
     unsigned long long *dev_counts = nullptr;   // 2 per slot: accepted, visits
@@ -64,7 +70,9 @@ struct hrr_server {
     unsigned long long *dev_misc = nullptr;     // 2 per ring entry: cursor, flags
     unsigned long long *host_flags = nullptr;   // pinned, 1 per ring entry
     cudaEvent_t slice_done[kRing] = {};
+    cudaEvent_t setup_done[kRing] = {};          // after a slice's allocations, resets, copies
     bool slice_busy[kRing] = {};
+    uint64_t slice_seq[kRing] = {};             // order in which ring entries were filled
     std::vector<Job *> slice_jobs[kRing];
     std::vector<int> free_slots;
     std::deque<Job *> pending;
@@ -131,22 +139,10 @@ void admit(hrr_server *s) {
             continue;
         }
         if (s->used + j->bytes > s->budget) break;
-        void *p = nullptr;
-        if (j->bytes && cudaMallocAsync(&p, j->bytes, s->stream) != cudaSuccess) {
-            cudaGetLastError();
-            if (s->active.empty()) {  // nothing will free memory: give up on this job
-                s->pending.pop_front();
-                fail_job(s, j, HRR_ERR_OOM);
-                continue;
-            }
-            break;
-        }
         s->pending.pop_front();
-        j->pairs = static_cast<uint2 *>(p);
-        s->used += j->bytes;
+        s->used += j->bytes;  // the buffer itself is allocated on the job's first slice stream
         j->slot = s->free_slots.back();
         s->free_slots.pop_back();
-        cudaMemsetAsync(s->dev_counts + 2 * (size_t)j->slot, 0, 2 * sizeof(unsigned long long), s->stream);
         j->t_admit = Clock::now();
         j->admitted = true;
         s->active.push_back(j);
@@ -159,12 +155,28 @@ void admit(hrr_server *s) {
 // the queue allows, the next jobs' eyes fill the GPU while the older ones drain, and only a
 // few hierarchies are live in L2 at a time. Returns false when there was nothing to do.
 bool enqueue_slice(hrr_server *s, int k) {
+    cudaStream_t st = s->slice_stream[k];
+    bool any = false;
+    for (Job *j : s->active) any |= !j->all_launched;
+    if (!any) return false;
+    // A job continuing from the previous slice (other stream) needs that slice's setup
+    // (its buffer allocation and counter reset) to have happened first.
+    if (s->last_slice >= 0 && s->last_slice != k) cudaStreamWaitEvent(st, s->setup_done[s->last_slice], 0);
     std::vector<Job *> work;
     std::vector<uint32_t> takes;
     uint64_t budget = s->slice_eyes;
     for (Job *j : s->active) {
         if (j->all_launched) continue;
         if (budget == 0) break;
+        if (j->next_eye == 0) {  // first slice of the job: its buffer and counters
+            void *p = nullptr;
+            if (j->bytes && cudaMallocFromPoolAsync(&p, j->bytes, s->pool, st) != cudaSuccess) {
+                cudaGetLastError();
+                j->status = HRR_ERR_OOM;  // completes (with no pairs) like any other job
+            }
+            j->pairs = static_cast<uint2 *>(p);
+            cudaMemsetAsync(s->dev_counts + 2 * (size_t)j->slot, 0, 2 * sizeof(unsigned long long), st);
+        }
         const uint32_t take = (uint32_t)std::min<uint64_t>(budget, j->desc.n_eyes - j->next_eye);
         work.push_back(j);
         takes.push_back(take);
@@ -186,7 +198,7 @@ bool enqueue_slice(hrr_server *s, int k) {
         d.perm = j->desc.tree->perm;
         d.tile = j->tile; d.tile_w = j->tile_w; d.tile_h = j->tile_h;
         d.pairs = j->pairs;
-        d.cap = j->desc.cap;
+        d.cap = j->pairs ? j->desc.cap : 0;  // no buffer (allocation failed): count only
         d.counts = s->dev_counts + 2 * (size_t)j->slot;
         d.eye_visits = nullptr;
         d.n_lights = j->desc.tree->n;
@@ -198,22 +210,29 @@ bool enqueue_slice(hrr_server *s, int k) {
         j->next_eye += take;
         if (j->next_eye == j->desc.n_eyes) finishing.push_back(j);
     }
-    cudaMemcpyAsync(s->dev_frames[k], h, sizeof(hrr_cull_frame_t) * n, cudaMemcpyHostToDevice, s->stream);
-    cudaMemsetAsync(s->dev_misc + 2 * k, 0, 2 * sizeof(unsigned long long), s->stream);
+    cudaMemcpyAsync(s->dev_frames[k], h, sizeof(hrr_cull_frame_t) * n, cudaMemcpyHostToDevice, st);
+    cudaMemsetAsync(s->dev_misc + 2 * k, 0, 2 * sizeof(unsigned long long), st);
+    cudaEventRecord(s->setup_done[k], st);
     if (hrr_cull_batch_enqueue(s->sm_count, s->dev_frames[k], n, cursor, s->dev_misc + 2 * k,
-                               s->dev_misc + 2 * k + 1, s->variant, s->stream) == cudaSuccess && cursor)
+                               s->dev_misc + 2 * k + 1, s->tuning, st) == cudaSuccess && cursor)
         ++s->launches;
     cudaMemcpyAsync(&s->host_flags[k], s->dev_misc + 2 * k + 1, sizeof(unsigned long long),
-                    cudaMemcpyDeviceToHost, s->stream);
+                    cudaMemcpyDeviceToHost, st);
+    if (!finishing.empty() && s->last_slice >= 0 && s->last_slice != k)
+        // a finishing job may also have eyes in the previous slice, on the other stream:
+        // its results are complete only after both
+        cudaStreamWaitEvent(st, s->slice_done[s->last_slice], 0);
     for (Job *j : finishing) {
         cudaMemcpyAsync(s->host_counts + 2 * (size_t)j->slot, s->dev_counts + 2 * (size_t)j->slot,
-                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream);
-        cudaEventRecord(j->done_ev, s->stream);
+                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        cudaEventRecord(j->done_ev, st);
         j->all_launched = true;
     }
     s->slice_jobs[k] = work;
-    cudaEventRecord(s->slice_done[k], s->stream);
+    cudaEventRecord(s->slice_done[k], st);
     s->slice_busy[k] = true;
+    s->slice_seq[k] = s->slices;
+    s->last_slice = k;
     ++s->slices;
     return true;
 }
@@ -234,7 +253,7 @@ void run(hrr_server *s) {
         // Nothing to enqueue now: wait for the oldest busy slice, or for new work.
         int busy = -1;
         for (int i = 0; i < kRing; ++i)
-            if (s->slice_busy[i]) { busy = i; break; }
+            if (s->slice_busy[i] && (busy < 0 || s->slice_seq[i] < s->slice_seq[busy])) busy = i;
         bool finishing = false;
         for (Job *j : s->active) finishing |= j->all_launched;
         if (busy >= 0 || finishing) {
@@ -256,17 +275,22 @@ void destroy_resources(hrr_server *s) {
         if (j->done_ev) cudaEventDestroy(j->done_ev);
         delete j;
     }
-    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (int k = 0; k < kRing; ++k)
+        if (s->slice_stream[k]) cudaStreamSynchronize(s->slice_stream[k]);
+    for (int k = 1; k < kRing; ++k)
+        if (s->slice_stream[k]) cudaStreamDestroy(s->slice_stream[k]);
     for (int k = 0; k < kRing; ++k) {
         if (s->dev_frames[k]) cudaFree(s->dev_frames[k]);
         if (s->host_frames[k]) cudaFreeHost(s->host_frames[k]);
         if (s->slice_done[k]) cudaEventDestroy(s->slice_done[k]);
+        if (s->setup_done[k]) cudaEventDestroy(s->setup_done[k]);
     }
     if (s->dev_counts) cudaFree(s->dev_counts);
     if (s->host_counts) cudaFreeHost(s->host_counts);
     if (s->dev_misc) cudaFree(s->dev_misc);
     if (s->host_flags) cudaFreeHost(s->host_flags);
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
 }
 
@@ -286,24 +310,27 @@ void fill_result(const Job *j, hrr_job_result *r) {
 extern "C" {
 
 int hrr_server_create(hrr_ctx *ctx, uint64_t hbm_budget_bytes, uint32_t slice_eyes,
-                      uint32_t max_jobs, int rangemin_variant, hrr_server **out) {
+                      uint32_t max_jobs, const hrr_tuning *tuning, hrr_server **out) {
     if (!ctx) return HRR_ERR_INVALID_ARG;
     if (!out) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (max_jobs == 0 || max_jobs > 65535)
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "max_jobs must be in [1, 65535]");
-    if (rangemin_variant < 0 || rangemin_variant > 2)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2");
+    const hrr_tuning tn = tuning ? *tuning : hrr_tuning{};
+    if (!hrr_tuning_valid(tn)) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "invalid tuning");
     hrr_server *s = new (std::nothrow) hrr_server();
     if (!s) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of the server");
     s->device = ctx->device;
     s->sm_count = ctx->sm_count;
-    s->variant = rangemin_variant;
+    s->tuning = hrr_tuning_normalized(tn);
     s->budget = hbm_budget_bytes;
-    s->slice_eyes = slice_eyes ? slice_eyes : (1u << 19);
+    s->slice_eyes = slice_eyes ? slice_eyes : (1u << 20);
     s->max_slots = max_jobs;
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    s->slice_stream[0] = s->stream;
+    for (int k = 1; k < kRing && e == cudaSuccess; ++k)
+        e = cudaStreamCreateWithFlags(&s->slice_stream[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->dev_counts, sizeof(unsigned long long) * 2 * max_jobs);
     if (e == cudaSuccess) e = cudaMallocHost(&s->host_counts, sizeof(unsigned long long) * 2 * max_jobs);
     if (e == cudaSuccess) e = cudaMalloc(&s->dev_misc, sizeof(unsigned long long) * 2 * kRing);
@@ -312,10 +339,28 @@ int hrr_server_create(hrr_ctx *ctx, uint64_t hbm_budget_bytes, uint32_t slice_ey
         e = cudaMalloc(&s->dev_frames[k], sizeof(hrr_cull_frame_t) * max_jobs);
         if (e == cudaSuccess) e = cudaMallocHost(&s->host_frames[k], sizeof(hrr_cull_frame_t) * max_jobs);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->slice_done[k], cudaEventDisableTiming | cudaEventBlockingSync);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->setup_done[k], cudaEventDisableTiming);
     }
     if (e != cudaSuccess) {
         destroy_resources(s);
         return hrr_cuda_fail(ctx, e, "server allocation");
+    }
+    if (e == cudaSuccess) {
+        // A pool of its own, holding on to freed job outputs up to the budget: a new job's
+        // buffer then reuses mapped memory instead of mapping fresh pages.
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = ctx->device;
+        e = cudaMemPoolCreate(&s->pool, &props);
+        if (e == cudaSuccess) {
+            uint64_t keep = hbm_budget_bytes;
+            e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
+    if (e != cudaSuccess) {
+        destroy_resources(s);
+        return hrr_cuda_fail(ctx, e, "server memory pool");
     }
     for (uint32_t i = 0; i < max_jobs; ++i) s->free_slots.push_back((int)(max_jobs - 1 - i));
     try {
