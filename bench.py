@@ -214,7 +214,7 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             batched = run_batched(ctx, frames, stream, dev)
             if args.served_jobs > 0:
-                tn = {k: batched["tuning"][k] for k in ("rangemin_variant", "blocks_per_sm", "refill_below")}
+                tn = {k: batched["tuning"][k] for k in ("rangemin_variant", "blocks_per_sm")}
                 served = {"config": run_served(ctx, frames, stream, dev, args.served_jobs, 200.0, tuning=tn)}
                 # the same at a load the GPU can sustain: 70% of its job-by-job capacity
                 cap_jobs = args.batch_frames / (batched["plain_job_by_job"]["ms"] / 1e3)
@@ -258,7 +258,7 @@ def run_ours(args):
 # 1.963 internal child tests x 27 float ops (bound + cull predicate) + 0.977 range minima x
 # 51 integer ops + 0.774 inherited minima x 2 + 0.037 leaf tests x 17.
 OPS_PER_VISIT = 1.963 * 27 + 0.977 * 51 + 0.774 * 2 + 0.037 * 17
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_kernel_frame_1920x1080.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_1920x1080.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
                   for f in ("hrr_cull.cu", "hrr_internal.cuh")]
 
@@ -327,7 +327,7 @@ def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk):
         "frac": achieved / peak,
         "traffic": profiled_traffic(),
         "peak_kind": f"derived from {sms} SMs x 128 lanes x {mhz:.0f} MHz ({kind} sm_max_mhz)",
-        "kernel": "cull_kernel",
+        "kernel": "cull_single_kernel",
         "kernel_ms": cull_ms,
         "ops_per_visit": OPS_PER_VISIT,
         "node_visits_per_s": V / sec,

@@ -107,18 +107,15 @@ typedef struct hrr_cull_opts {
     /* added (mod 2^32) to every eye's shift: the sample offset psi(n) of the adaptive
      * sampling variant (Sec. 3), absorbed into the shift; 0 for the plain method */
     uint32_t shift_offset;
-    /* launch shape (results do not depend on it): resident blocks per SM of the persistent
-     * grid (0 = as many as fit), and the number of busy lanes below which a warp refills
-     * its idle lanes with new eyes (1..32, 0 = 29); see hrr_autotune */
+    /* launch shape (results do not depend on it): resident 256-thread blocks per SM of the
+     * persistent grid, 0 = as many as fit (at most 64); see hrr_autotune */
     uint32_t blocks_per_sm;
-    uint32_t refill_below;
 } hrr_cull_opts;
 
 /* Launch parameters of the traversal (see hrr_cull_opts); none changes any result. */
 typedef struct hrr_tuning {
     int rangemin_variant;
     uint32_t blocks_per_sm;
-    uint32_t refill_below;
 } hrr_tuning;
 
 /* ---- context --------------------------------------------------------------------------- */
@@ -322,8 +319,8 @@ int hrr_server_destroy(hrr_server *server);
 
 /* ---- autotuning ---------------------------------------------------------------------- */
 
-/* Time every candidate launch shape (range-minimum variants 0 and 2, 2..4 blocks per SM,
- * refill thresholds 24 / 29 / 32) on the given eyes (a sample of a workload's size class)
+/* Time every candidate launch shape (range-minimum variants 0 and 2; 4, 5 or 6 resident
+ * blocks per SM, capped by what fits) on the given eyes (a sample of a workload's size class)
  * and return the fastest in *best (its median time in *best_ms, may be NULL). dev_pairs /
  * cap as in hrr_cull and large enough for the sample. Results of every candidate are
  * identical; only the time differs. Synchronous. */

@@ -84,24 +84,20 @@ class hrr_server_info(C.Structure):
 
 class hrr_cull_opts(C.Structure):
     _fields_ = [("eye_visits", C.c_void_p), ("rangemin_variant", C.c_int),
-                ("shift_offset", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-                ("refill_below", C.c_uint32)]
+                ("shift_offset", C.c_uint32), ("blocks_per_sm", C.c_uint32)]
 
 
 class hrr_tuning(C.Structure):
-    _fields_ = [("rangemin_variant", C.c_int), ("blocks_per_sm", C.c_uint32),
-                ("refill_below", C.c_uint32)]
+    _fields_ = [("rangemin_variant", C.c_int), ("blocks_per_sm", C.c_uint32)]
 
     @classmethod
     def from_dict(cls, d):
         if d is None:
             return None
-        return cls(int(d.get("rangemin_variant", 0)), int(d.get("blocks_per_sm", 0)),
-                   int(d.get("refill_below", 0)))
+        return cls(int(d.get("rangemin_variant", 0)), int(d.get("blocks_per_sm", 0)))
 
     def to_dict(self):
-        return {"rangemin_variant": int(self.rangemin_variant), "blocks_per_sm": int(self.blocks_per_sm),
-                "refill_below": int(self.refill_below)}
+        return {"rangemin_variant": int(self.rangemin_variant), "blocks_per_sm": int(self.blocks_per_sm)}
 
 
 _P = C.c_void_p
@@ -225,7 +221,7 @@ class Context:
         cnt = _u64()
         t = tuning or {}
         opts = hrr_cull_opts(_ptr(eye_visits), int(t.get("rangemin_variant", rangemin_variant)),
-                             shift_offset, int(t.get("blocks_per_sm", 0)), int(t.get("refill_below", 0)))
+                             shift_offset, int(t.get("blocks_per_sm", 0)))
         st = hrr_cull_ex(self.handle, E, n, tree.handle, float(tau), C.byref(opts),
                          _ptr(pairs) if cap else None, cap, C.byref(cnt))
         if st not in (HRR_OK, HRR_ERR_OVERFLOW):
@@ -289,7 +285,7 @@ class Batch:
                 _ptr(fr["pairs"]) if fr["pairs"].shape[0] else None, int(fr["pairs"].shape[0]),
                 _ptr(fr.get("eye_visits")))
         h = _P()
-        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0, 0)
+        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0)
         ctx.check(hrr_batch_create(ctx.handle, arr, self.n, C.byref(tn), 1 if use_graph else 0,
                                    C.byref(h)))
         self.handle = h
@@ -329,7 +325,7 @@ class Server:
                  max_jobs: int = 1024, rangemin_variant: int = 0, tuning=None):
         self.ctx = ctx
         h = _P()
-        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0, 0)
+        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0)
         ctx.check(hrr_server_create(ctx.handle, int(hbm_budget_bytes), int(slice_eyes), int(max_jobs),
                                     C.byref(tn), C.byref(h)))
         self.handle = h

@@ -1,7 +1,7 @@
 """Per-size-class autotuning of the traversal's launch shape, cached in JSON.
 
 The traversal gives identical results for every launch shape (range-minimum variant,
-resident blocks per SM, lane-refill threshold); only its speed depends on the workload.
+resident blocks per SM); only its speed depends on the workload.
 ``Autotuner`` keys workloads by size class (bit lengths of N_l and N_e), tunes a class
 once on a sample of its eyes with ``hrr_autotune`` and stores the answer, so later
 frames, batches and servers of that class reuse it.
@@ -58,4 +58,4 @@ class Autotuner:
     def launch_fields(entry: dict | None) -> dict | None:
         if entry is None:
             return None
-        return {k: entry[k] for k in ("rangemin_variant", "blocks_per_sm", "refill_below")}
+        return {k: entry[k] for k in ("rangemin_variant", "blocks_per_sm")}

@@ -104,6 +104,7 @@ int hrr_destroy(hrr_ctx *ctx) {
     if (ctx->tile) cudaFree(ctx->tile);
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
+    if (ctx->spill) cudaFree(ctx->spill);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return HRR_OK;
@@ -225,8 +226,8 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
     if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
     hrr_cull_opts o{};
     if (opts) o = *opts;
-    if (o.rangemin_variant < 0 || o.rangemin_variant > 2 || o.refill_below > 32)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2 and refill_below <= 32");
+    if (o.rangemin_variant < 0 || o.rangemin_variant > 2 || o.blocks_per_sm > 64)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2 and blocks_per_sm <= 64");
     DeviceGuard g(ctx->device);
     return hrr_cull_impl(ctx, eyes, n_eyes, tree, tau, o, dev_pairs, cap, out_count);
 }

@@ -1,10 +1,12 @@
 // Batched culling: many frames (each its own eyes, hierarchy, tile, tau and output) in one
-// persistent traversal launch, optionally recorded once into a CUDA graph and replayed.
+// persistent traversal launch (one per HRR_CULL_MAX_FRAMES frames), optionally recorded once
+// into a CUDA graph and replayed.
 //
-// A batch keeps its frame descriptors, per-frame counters and the launch's eye cursor in
-// device memory. Replaying it resets the counters and runs the traversal over the eyes of
-// every frame; frames of very different sizes share the launch, so there is no per-frame
-// launch overhead or tail.
+// A batch keeps its frame descriptors on the host (they travel as kernel parameters) and its
+// per-frame counters, the launches' eye cursors and the device flags in device memory.
+// Replaying it resets the counters and runs the traversal over the eyes of every frame;
+// frames of very different sizes share a launch, so there is no per-frame launch overhead.
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -14,32 +16,45 @@ struct hrr_batch {
     uint32_t n_frames = 0;
     unsigned long long total = 0;
     hrr_tuning tuning{};
-    hrr_cull_frame_t *dev_frames = nullptr;
-    unsigned long long *dev_counts = nullptr;  // 2 per frame (accepted, visits), then cursor, flags
+    std::vector<hrr_cull_frame_t> desc;         // cursor offsets restart in every launch
+    struct Part {
+        uint32_t first = 0, count = 0;          // frames [first, first + count)
+        unsigned long long total = 0;           // their eyes
+        unsigned grid = 1;
+    };
+    std::vector<Part> parts;                    // one traversal launch each
+    uint32_t spill_cap = 0;                     // stack spill entries per warp
+    void *spill = nullptr;                      // stack spill area (launches run in order)
+    unsigned long long *dev_counts = nullptr;  // 2 per frame (accepted, visits), a cursor per part, flags
     unsigned long long *host_counts = nullptr; // pinned mirror
     std::vector<uint64_t> caps;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
+
+    size_t n_counters() const { return 2 * (size_t)n_frames + parts.size() + 1; }
 };
 
 namespace {
 
 int enqueue(hrr_ctx *ctx, hrr_batch *b, cudaStream_t st) {
-    const size_t bytes = sizeof(unsigned long long) * (2 * (size_t)b->n_frames + 2);
-    HRR_CUDA(ctx, cudaMemsetAsync(b->dev_counts, 0, bytes, st));
-    unsigned long long *misc = b->dev_counts + 2 * (size_t)b->n_frames;
-    HRR_CUDA(ctx, hrr_cull_batch_enqueue(ctx->sm_count, b->dev_frames, b->n_frames, b->total, misc,
-                                         misc + 1, b->tuning, st));
-    if (b->total) ++ctx->launches;
+    HRR_CUDA(ctx, cudaMemsetAsync(b->dev_counts, 0, sizeof(unsigned long long) * b->n_counters(), st));
+    unsigned long long *cursors = b->dev_counts + 2 * (size_t)b->n_frames;
+    unsigned long long *flags = cursors + b->parts.size();
+    for (size_t p = 0; p < b->parts.size(); ++p) {
+        const hrr_batch::Part &pt = b->parts[p];
+        HRR_CUDA(ctx, hrr_cull_batch_enqueue(pt.grid, b->desc.data() + pt.first, pt.count, pt.total, cursors + p,
+                                             flags, b->spill, b->spill_cap, b->tuning, st));
+        if (pt.total) ++ctx->launches;
+    }
     return HRR_OK;
 }
 
 void release(hrr_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
-    if (b->dev_frames) cudaFree(b->dev_frames);
     if (b->dev_counts) cudaFree(b->dev_counts);
     if (b->host_counts) cudaFreeHost(b->host_counts);
+    if (b->spill) cudaFree(b->spill);
     delete b;
 }
 
@@ -56,14 +71,15 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "n_frames must be in [1, 65535]");
     const hrr_tuning tn = tuning ? *tuning : hrr_tuning{};
     if (!hrr_tuning_valid(tn)) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "invalid tuning");
-    std::vector<hrr_cull_frame_t> desc(n_frames);
     hrr_batch *b = new (std::nothrow) hrr_batch();
     if (!b) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of the batch");
     b->n_frames = n_frames;
     b->tuning = hrr_tuning_normalized(tn);
     b->caps.resize(n_frames);
+    b->desc.resize(n_frames);
     DeviceGuard g(ctx->device);
     unsigned long long cursor = 0;
+    uint32_t height = 0;
     for (uint32_t i = 0; i < n_frames; ++i) {
         const hrr_frame &fr = frames[i];
         const char *bad = nullptr;
@@ -84,7 +100,13 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
             release(b);
             return hrr_fail(ctx, status, bad);
         }
-        hrr_cull_frame_t &d = desc[i];
+        if (i % HRR_CULL_MAX_FRAMES == 0) {  // a new launch
+            b->parts.push_back(hrr_batch::Part{});
+            b->parts.back().first = i;
+            cursor = 0;
+        }
+        hrr_batch::Part &pt = b->parts.back();
+        hrr_cull_frame_t &d = b->desc[i];
         d = hrr_cull_frame_t{};
         d.ex = fr.eyes.x; d.ey = fr.eyes.y; d.ez = fr.eyes.z; d.px = fr.eyes.px; d.py = fr.eyes.py;
         d.nodes = reinterpret_cast<const float4 *>(fr.tree->nodes);
@@ -101,22 +123,26 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
         d.eye_begin = 0;
         d.cursor_begin = cursor;
         cursor += fr.n_eyes;
+        ++pt.count;
+        pt.total = cursor;
+        b->total += fr.n_eyes;
         b->caps[i] = fr.cap;
+        height = std::max(height, fr.tree->height);
     }
-    b->total = cursor;
-    cudaError_t e = cudaMalloc(&b->dev_frames, sizeof(hrr_cull_frame_t) * n_frames);
-    if (e == cudaSuccess) e = cudaMalloc(&b->dev_counts, sizeof(unsigned long long) * (2 * (size_t)n_frames + 2));
-    if (e == cudaSuccess) e = cudaMallocHost(&b->host_counts, sizeof(unsigned long long) * (2 * (size_t)n_frames + 2));
+    unsigned grid_max = 1;
+    for (hrr_batch::Part &pt : b->parts) {
+        pt.grid = hrr_cull_grid(ctx->sm_count, b->tuning, true, pt.total);
+        grid_max = std::max(grid_max, pt.grid);
+    }
+    b->spill_cap = hrr_cull_spill_cap(height);
+    cudaError_t e = cudaMalloc(&b->spill, hrr_cull_spill_entries(grid_max, height) * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMalloc(&b->dev_counts, sizeof(unsigned long long) * b->n_counters());
+    if (e == cudaSuccess) e = cudaMallocHost(&b->host_counts, sizeof(unsigned long long) * b->n_counters());
     if (e != cudaSuccess) {
         release(b);
         return hrr_cuda_fail(ctx, e, "batch allocation");
     }
-    for (uint32_t i = 0; i < n_frames; ++i) desc[i].counts = b->dev_counts + 2 * (size_t)i;
-    e = cudaMemcpy(b->dev_frames, desc.data(), sizeof(hrr_cull_frame_t) * n_frames, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        release(b);
-        return hrr_cuda_fail(ctx, e, "batch descriptor upload");
-    }
+    for (uint32_t i = 0; i < n_frames; ++i) b->desc[i].counts = b->dev_counts + 2 * (size_t)i;
     if (use_graph) {
         // Record [reset counters, traversal] once on a private stream; replays go to ctx->stream.
         cudaGraph_t graph = nullptr;
@@ -145,7 +171,7 @@ int hrr_batch_launch(hrr_ctx *ctx, hrr_batch *b) {
     DeviceGuard g(ctx->device);
     if (b->exec) {
         HRR_CUDA(ctx, cudaGraphLaunch(b->exec, ctx->stream));
-        ++ctx->launches;
+        for (const hrr_batch::Part &pt : b->parts) ctx->launches += pt.total ? 1 : 0;
         return HRR_OK;
     }
     return enqueue(ctx, b, ctx->stream);
@@ -154,7 +180,7 @@ int hrr_batch_launch(hrr_ctx *ctx, hrr_batch *b) {
 int hrr_batch_results(hrr_ctx *ctx, hrr_batch *b, uint64_t *counts, uint64_t *visits) {
     if (!ctx || !b) return HRR_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
-    const size_t n = 2 * (size_t)b->n_frames + 2;
+    const size_t n = b->n_counters();
     HRR_CUDA(ctx, cudaMemcpyAsync(b->host_counts, b->dev_counts, sizeof(unsigned long long) * n,
                                   cudaMemcpyDeviceToHost, ctx->stream));
     HRR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -31,6 +31,9 @@ struct hrr_ctx {
     std::vector<cudaEvent_t> ev_start, ev_stop;  // recorded pairs, in order
     std::vector<cudaEvent_t> ev_pool;
     int sm_count = 0;
+    // traversal stack spill area (grown on demand by hrr_cull)
+    void *spill = nullptr;
+    size_t spill_entries = 0;
     std::string err;
 };
 
@@ -84,27 +87,37 @@ struct hrr_cull_frame_t {
     unsigned long long cursor_begin; // where the frame's eyes start on the launch's cursor
 };
 
-// Launch parameters with the library defaults filled in (refill_below 0 -> 29).
-inline hrr_tuning hrr_tuning_normalized(hrr_tuning t) {
-    if (t.refill_below == 0 || t.refill_below > 32) t.refill_below = 29;
-    return t;
-}
+// Launch parameters with the library defaults filled in (nothing to fill in today).
+inline hrr_tuning hrr_tuning_normalized(hrr_tuning t) { return t; }
 inline hrr_tuning hrr_tuning_of(const hrr_cull_opts &o) {
     hrr_tuning t{};
     t.rangemin_variant = o.rangemin_variant;
     t.blocks_per_sm = o.blocks_per_sm;
-    t.refill_below = o.refill_below;
     return hrr_tuning_normalized(t);
 }
 inline bool hrr_tuning_valid(const hrr_tuning &t) {
-    return t.rangemin_variant >= 0 && t.rangemin_variant <= 2 && t.refill_below <= 32;
+    return t.rangemin_variant >= 0 && t.rangemin_variant <= 2 && t.blocks_per_sm <= 64;
 }
 
-// Enqueue one batched traversal on st (hrr_cull.cu); a no-op when total == 0. The cursor
-// must be zero when the kernel starts. sm_count sizes the persistent grid.
-cudaError_t hrr_cull_batch_enqueue(int sm_count, const hrr_cull_frame_t *dev_frames, uint32_t n_frames,
+// The traversal (hrr_cull.cu). Threads per block of its persistent grid, and frames of one
+// batched launch (their descriptors are kernel parameters: 128 x 128 bytes):
+#define HRR_CULL_THREADS 256
+#define HRR_CULL_MAX_FRAMES 128u
+// Blocks of a traversal launch over `total` eyes (a whole number per SM, at most one warp per
+// eye), for the single-frame or the batched kernel.
+unsigned hrr_cull_grid(int sm_count, const hrr_tuning &tuning, bool batch, unsigned long long total);
+// Stack entries per warp that the spill area must hold for trees of the given height, and
+// the area's entries (8 bytes each) for a grid.
+uint32_t hrr_cull_spill_cap(uint32_t height);
+size_t hrr_cull_spill_entries(unsigned grid, uint32_t height);
+// Enqueue one batched traversal over n_frames <= HRR_CULL_MAX_FRAMES frames (host array, copied
+// into the launch) on st; a no-op when total == 0. The cursor and flags must be zero when the
+// kernel starts. spill holds hrr_cull_spill_entries(grid, height) entries for the tallest tree
+// of the frames, spill_cap = hrr_cull_spill_cap(height).
+cudaError_t hrr_cull_batch_enqueue(unsigned grid, const hrr_cull_frame_t *frames, uint32_t n_frames,
                                    unsigned long long total, unsigned long long *cursor,
-                                   unsigned long long *flags, const hrr_tuning &tuning, cudaStream_t st);
+                                   unsigned long long *flags, void *spill, uint32_t spill_cap,
+                                   const hrr_tuning &tuning, cudaStream_t st);
 
 // Traversal timing (hrr_abi.cu)
 void hrr_timing_begin(hrr_ctx *ctx);

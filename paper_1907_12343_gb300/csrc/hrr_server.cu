@@ -18,6 +18,7 @@
 // which other jobs shared its slices (each frame of a slice is traversed exactly as
 // hrr_cull would).
 #include <chrono>
+#include <algorithm>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -65,9 +66,11 @@ struct hrr_server {
     uint32_t slice_eyes = 0, max_slots = 0;
     unsigned long long *dev_counts = nullptr;   // 2 per slot: accepted, visits
     unsigned long long *host_counts = nullptr;  // pinned copies, 2 per slot
-    hrr_cull_frame_t *dev_frames[kRing] = {};
-    hrr_cull_frame_t *host_frames[kRing] = {};  // pinned staging of slice descriptors
+    std::vector<hrr_cull_frame_t> host_frames[kRing];  // slice descriptors (kernel parameters)
     unsigned long long *dev_misc = nullptr;     // 2 per ring entry: cursor, flags
+    unsigned grid_max = 1;                      // blocks of a full slice's traversal
+    void *spill[kRing] = {};                    // traversal stack spill area per ring entry
+    uint32_t spill_height = 0;                  // tallest tree the spill areas are sized for
     unsigned long long *host_flags = nullptr;   // pinned, 1 per ring entry
     cudaEvent_t slice_done[kRing] = {};
     cudaEvent_t setup_done[kRing] = {};          // after a slice's allocations, resets, copies
@@ -150,6 +153,31 @@ void admit(hrr_server *s) {
     }
 }
 
+// Size both ring entries' stack spill areas for trees up to the given height (once per
+// taller tree; waits for the slices in flight). False if the memory is not there.
+bool ensure_spill(hrr_server *s, uint32_t height) {
+    if (height <= s->spill_height && s->spill[0]) return true;
+    for (int k = 0; k < kRing; ++k) cudaStreamSynchronize(s->slice_stream[k]);
+    const size_t bytes = hrr_cull_spill_entries(s->grid_max, height) * sizeof(uint2);
+    for (int k = 0; k < kRing; ++k) {
+        if (s->spill[k]) cudaFree(s->spill[k]);
+        s->spill[k] = nullptr;
+    }
+    s->spill_height = 0;
+    for (int k = 0; k < kRing; ++k) {
+        if (cudaMalloc(&s->spill[k], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            for (int i = 0; i <= k; ++i) {
+                if (s->spill[i]) cudaFree(s->spill[i]);
+                s->spill[i] = nullptr;
+            }
+            return false;
+        }
+    }
+    s->spill_height = height;
+    return true;
+}
+
 // Enqueue one slice: up to slice_eyes of the admitted jobs' remaining eyes, taken in
 // admission order (the oldest job first). Each job thus finishes as early as its place in
 // the queue allows, the next jobs' eyes fill the GPU while the older ones drain, and only a
@@ -167,7 +195,7 @@ bool enqueue_slice(hrr_server *s, int k) {
     uint64_t budget = s->slice_eyes;
     for (Job *j : s->active) {
         if (j->all_launched) continue;
-        if (budget == 0) break;
+        if (budget == 0 || work.size() == HRR_CULL_MAX_FRAMES) break;
         if (j->next_eye == 0) {  // first slice of the job: its buffer and counters
             void *p = nullptr;
             if (j->bytes && cudaMallocFromPoolAsync(&p, j->bytes, s->pool, st) != cudaSuccess) {
@@ -183,7 +211,10 @@ bool enqueue_slice(hrr_server *s, int k) {
         budget -= take;
     }
     if (work.empty()) return false;
-    hrr_cull_frame_t *h = s->host_frames[k];
+    uint32_t height = 0;
+    for (Job *j : work) height = std::max(height, j->desc.tree->height);
+    const bool have_spill = ensure_spill(s, height);
+    hrr_cull_frame_t *h = s->host_frames[k].data();
     unsigned long long cursor = 0;
     uint32_t n = 0;
     std::vector<Job *> finishing;
@@ -210,12 +241,16 @@ bool enqueue_slice(hrr_server *s, int k) {
         j->next_eye += take;
         if (j->next_eye == j->desc.n_eyes) finishing.push_back(j);
     }
-    cudaMemcpyAsync(s->dev_frames[k], h, sizeof(hrr_cull_frame_t) * n, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(s->dev_misc + 2 * k, 0, 2 * sizeof(unsigned long long), st);
     cudaEventRecord(s->setup_done[k], st);
-    if (hrr_cull_batch_enqueue(s->sm_count, s->dev_frames[k], n, cursor, s->dev_misc + 2 * k,
-                               s->dev_misc + 2 * k + 1, s->tuning, st) == cudaSuccess && cursor)
-        ++s->launches;
+    if (!have_spill) {
+        for (Job *j : work) j->status = HRR_ERR_OOM;  // completes with no pairs
+    } else if (cursor) {
+        const unsigned grid = hrr_cull_grid(s->sm_count, s->tuning, true, cursor);
+        if (hrr_cull_batch_enqueue(grid, h, n, cursor, s->dev_misc + 2 * k, s->dev_misc + 2 * k + 1,
+                                   s->spill[k], hrr_cull_spill_cap(s->spill_height), s->tuning, st) == cudaSuccess)
+            ++s->launches;
+    }
     cudaMemcpyAsync(&s->host_flags[k], s->dev_misc + 2 * k + 1, sizeof(unsigned long long),
                     cudaMemcpyDeviceToHost, st);
     if (!finishing.empty() && s->last_slice >= 0 && s->last_slice != k)
@@ -280,8 +315,7 @@ void destroy_resources(hrr_server *s) {
     for (int k = 1; k < kRing; ++k)
         if (s->slice_stream[k]) cudaStreamDestroy(s->slice_stream[k]);
     for (int k = 0; k < kRing; ++k) {
-        if (s->dev_frames[k]) cudaFree(s->dev_frames[k]);
-        if (s->host_frames[k]) cudaFreeHost(s->host_frames[k]);
+        if (s->spill[k]) cudaFree(s->spill[k]);
         if (s->slice_done[k]) cudaEventDestroy(s->slice_done[k]);
         if (s->setup_done[k]) cudaEventDestroy(s->setup_done[k]);
     }
@@ -325,6 +359,7 @@ int hrr_server_create(hrr_ctx *ctx, uint64_t hbm_budget_bytes, uint32_t slice_ey
     s->tuning = hrr_tuning_normalized(tn);
     s->budget = hbm_budget_bytes;
     s->slice_eyes = slice_eyes ? slice_eyes : (1u << 20);
+    s->grid_max = hrr_cull_grid(ctx->sm_count, s->tuning, true, s->slice_eyes);
     s->max_slots = max_jobs;
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
@@ -336,9 +371,8 @@ int hrr_server_create(hrr_ctx *ctx, uint64_t hbm_budget_bytes, uint32_t slice_ey
     if (e == cudaSuccess) e = cudaMalloc(&s->dev_misc, sizeof(unsigned long long) * 2 * kRing);
     if (e == cudaSuccess) e = cudaMallocHost(&s->host_flags, sizeof(unsigned long long) * kRing);
     for (int k = 0; k < kRing && e == cudaSuccess; ++k) {
-        e = cudaMalloc(&s->dev_frames[k], sizeof(hrr_cull_frame_t) * max_jobs);
-        if (e == cudaSuccess) e = cudaMallocHost(&s->host_frames[k], sizeof(hrr_cull_frame_t) * max_jobs);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->slice_done[k], cudaEventDisableTiming | cudaEventBlockingSync);
+        s->host_frames[k].resize(HRR_CULL_MAX_FRAMES);
+        e = cudaEventCreateWithFlags(&s->slice_done[k], cudaEventDisableTiming | cudaEventBlockingSync);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->setup_done[k], cudaEventDisableTiming);
     }
     if (e != cudaSuccess) {

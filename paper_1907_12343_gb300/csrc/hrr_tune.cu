@@ -1,7 +1,7 @@
 // Autotuning of the traversal's launch shape.
 //
 // The traversal's results do not depend on its launch parameters (range-minimum variant,
-// resident blocks per SM, lane-refill threshold), only its speed does. hrr_autotune runs
+// resident blocks per SM), only its speed does. hrr_autotune runs
 // every candidate on a caller-given eye sample and keeps the fastest; a caller (the Python
 // autotuner) caches one answer per size class of workload.
 #include <algorithm>
@@ -20,17 +20,15 @@ extern "C" int hrr_autotune(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const 
     HRR_CUDA(ctx, cudaEventCreate(&a));
     HRR_CUDA(ctx, cudaEventCreate(&b));
     const int variants[] = {0, 2};
-    const uint32_t blocks[] = {2, 3, 4};
-    const uint32_t refills[] = {24, 29, 32};
+    const uint32_t blocks[] = {4, 5, 6};
     double best_t = 1e300;
     int status = HRR_OK;
     for (int v : variants) {
         for (uint32_t bl : blocks) {
-            for (uint32_t rf : refills) {
+            {
                 hrr_cull_opts o{};
                 o.rangemin_variant = v;
                 o.blocks_per_sm = bl;
-                o.refill_below = rf;
                 std::vector<double> t;
                 for (int rep = 0; rep < 4 && status == HRR_OK; ++rep) {
                     uint64_t count = 0;
@@ -49,7 +47,6 @@ extern "C" int hrr_autotune(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const 
                     best_t = med;
                     best->rangemin_variant = v;
                     best->blocks_per_sm = bl;
-                    best->refill_below = rf;
                 }
             }
         }

@@ -17,7 +17,7 @@ class FakeCtx:
 
     def autotune(self, x, y, z, px, py, tree, tau, pairs):
         self.calls.append(int(x.numel()))
-        return {"rangemin_variant": 2, "blocks_per_sm": 3, "refill_below": 24}, 1.25
+        return {"rangemin_variant": 2, "blocks_per_sm": 5}, 1.25
 
 
 def _eyes(n):
@@ -37,7 +37,7 @@ def test_tune_once_then_cached(tmp_path):
     at = Autotuner(ctx, cache_path=path, sample_eyes=1000)
     e = at.tune(*_eyes(5000), None, 1.0, n_lights=70000)
     assert ctx.calls == [1000]  # tuned on the bounded sample
-    assert Autotuner.launch_fields(e) == {"rangemin_variant": 2, "blocks_per_sm": 3, "refill_below": 24}
+    assert Autotuner.launch_fields(e) == {"rangemin_variant": 2, "blocks_per_sm": 5}
     assert e["sample_ms"] == 1.25
     again = at.tune(*_eyes(6000), None, 1.0, n_lights=66000)  # same class
     assert again == e and ctx.calls == [1000]

@@ -125,3 +125,41 @@ def test_batch_validation(ctx):
     assert e.value.status == hrr.HRR_ERR_INVALID_ARG
     fr["tree"].free()
     c.close()
+
+
+def test_more_frames_than_one_launch_holds(ctx):
+    # 300 frames (three launches of at most 128 frames) over two shared hierarchies, each
+    # frame with its own sample offset: every frame equals its plain cull
+    import torch
+
+    import paper_1907_12343_gb300 as hrr
+    scenes = [dict(synth.scene_uniform(n_lights=700, grid_w=8, grid_h=8, tile_w=8, tile_h=8, seed=31)),
+              dict(synth.scene_frame(width=12, height=7, n_lights=3001, tile_w=16, tile_h=16, seed=32))]
+    up = []
+    for s in scenes:
+        g = upload_scene(s)
+        up.append((s, g, ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"]),
+                   torch.from_numpy(np.ascontiguousarray(s["tile"]).view(np.int32)).to(dev())))
+    frames, want = [], []
+    for k in range(300):
+        s, g, tree, tile = up[k % 2]
+        off = (k * 0x9E3779B9) & 0xFFFFFFFF
+        ctx.set_shift_tile(s["tile"])
+        st, cnt, pairs, _ = run_cull(ctx, g, tree, float(s["tau"]), shift_offset=off)
+        assert st == 0
+        want.append(sorted_pairs(pairs))
+        frames.append({"x": g["ex"], "y": g["ey"], "z": g["ez"], "px": g["px"], "py": g["py"], "tree": tree,
+                       "tau": float(s["tau"]), "tile": tile, "shift_offset": off,
+                       "pairs": torch.empty((cnt + 8, 2), dtype=torch.int32, device=dev())})
+    launches0 = ctx.launch_count()
+    b = hrr.Batch(ctx, frames, use_graph=True)
+    b.launch()
+    st, counts, _ = b.results()
+    assert st == hrr.HRR_OK
+    assert ctx.launch_count() - launches0 == 3
+    for fr, w, c in zip(frames, want, counts):
+        assert c == len(w)
+        assert np.array_equal(sorted_pairs(fr["pairs"][:c].cpu().numpy().view(np.uint32)), w)
+    b.destroy()
+    for _, _, tree, _ in up:
+        tree.free()
