@@ -110,6 +110,9 @@ typedef struct hrr_cull_opts {
     /* launch shape (results do not depend on it): resident 256-thread blocks per SM of the
      * persistent grid, 0 = as many as fit (at most 64); see hrr_autotune */
     uint32_t blocks_per_sm;
+    /* sample index n: selects layer n mod d of a space-time tile (hrr_set_shift_tile_3d);
+     * 0 for a plain tile */
+    uint32_t sample_index;
 } hrr_cull_opts;
 
 /* Launch parameters of the traversal (see hrr_cull_opts); none changes any result. */
@@ -192,8 +195,15 @@ int hrr_build_light_tree_static(hrr_lights lights, uint32_t n_lights, hrr_node *
 
 /* Copy a w x h tile of uint32 shifts (row-major, host memory) into the context. The
  * eye at pixel (px, py) uses tile[(py mod h) * w + (px mod w)]. 1 <= w, h <= 65536.
- * Synchronises the context stream. */
+ * Synchronises the context stream. Same as hrr_set_shift_tile_3d with d = 1. */
 int hrr_set_shift_tile(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, uint32_t h);
+
+/* A space-time tile psi(j, n) (Sec. 3): d layers of w x h shifts (layer-major, then
+ * row-major). Sample n of the eye at pixel (px, py) uses
+ * tile[((n mod d) * h + (py mod h)) * w + (px mod w)]; the sample index n is the
+ * sample_index of hrr_cull_opts, hrr_frame or hrr_job. 1 <= w, h <= 65536, 1 <= d <= 65536,
+ * w * h * d <= 2^30. Synchronises the context stream. */
+int hrr_set_shift_tile_3d(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, uint32_t h, uint32_t d);
 
 /* ---- culling (Sec. 1: hierarchical Russian roulette with QMC sequences) ----------------- */
 
@@ -228,6 +238,8 @@ typedef struct hrr_frame {
     uint32_t *dev_pairs;        /* 2 * cap uint32 of device memory, 8-byte aligned */
     uint64_t cap;
     uint32_t *eye_visits;       /* optional per-eye visit counts (device, n_eyes), or NULL */
+    uint32_t tile_d;            /* layers of dev_tile (0 means 1); ignored for the context tile */
+    uint32_t sample_index;      /* layer sample_index mod d of the frame's tile */
 } hrr_frame;
 
 typedef struct hrr_batch hrr_batch; /* opaque, library-owned */
@@ -266,6 +278,8 @@ typedef struct hrr_job {
     float tau;
     uint32_t shift_offset;
     uint64_t cap;               /* output pairs to reserve */
+    uint32_t tile_d;            /* layers of dev_tile (0 means 1); ignored for the context tile */
+    uint32_t sample_index;      /* layer sample_index mod d of the job's tile */
 } hrr_job;
 
 typedef struct hrr_job_result {

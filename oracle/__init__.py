@@ -241,11 +241,20 @@ class Tree:
             self._t = None
 
 
-def _cull(fn, tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0):
+def spacetime_layer(tile, sample_index: int = 0) -> np.ndarray:
+    """The shifts of sample n: a (h, w) tile is used as is; a (d, h, w) space-time tile
+    psi(j, n) (Sec. 3, the 3D-tile option) gives layer n mod d."""
+    tile = np.asarray(tile, dtype=np.uint32)
+    if tile.ndim == 3:
+        return tile[int(sample_index) % tile.shape[0]]
+    return tile
+
+
+def _cull(fn, tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, sample_index=0):
     eye_pos = np.ascontiguousarray(eye_pos, dtype=np.float32).reshape(-1, 3)
     px = np.ascontiguousarray(px, dtype=np.uint16)
     py = np.ascontiguousarray(py, dtype=np.uint16)
-    tile = np.ascontiguousarray(tile, dtype=np.uint32)
+    tile = np.ascontiguousarray(spacetime_layer(tile, sample_index), dtype=np.uint32)
     h, w = tile.shape
     ids = None if eye_ids is None else np.ascontiguousarray(eye_ids, dtype=np.uint32)
     n_e = len(eye_pos)
@@ -271,14 +280,14 @@ def _cull(fn, tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0):
     return out
 
 
-def cull_flat(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0):
+def cull_flat(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, sample_index=0):
     """Every (eye, light) pair tested: the definition of the accepted set."""
-    return _cull(lib().or_cull_flat, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads)
+    return _cull(lib().or_cull_flat, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads, sample_index)
 
 
-def cull_hier(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0):
+def cull_hier(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, sample_index=0):
     """Hierarchical traversal with per-eye visit counts; must equal ``cull_flat``."""
-    return _cull(lib().or_cull_hier, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads)
+    return _cull(lib().or_cull_hier, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads, sample_index)
 
 
 def max_threads() -> int:

@@ -62,13 +62,15 @@ class hrr_frame(C.Structure):
     _fields_ = [("eyes", hrr_eyes), ("n_eyes", C.c_uint32), ("tree", C.c_void_p),
                 ("dev_tile", C.c_void_p), ("tile_w", C.c_uint32), ("tile_h", C.c_uint32),
                 ("tau", C.c_float), ("shift_offset", C.c_uint32), ("dev_pairs", C.c_void_p),
-                ("cap", C.c_uint64), ("eye_visits", C.c_void_p)]
+                ("cap", C.c_uint64), ("eye_visits", C.c_void_p), ("tile_d", C.c_uint32),
+                ("sample_index", C.c_uint32)]
 
 
 class hrr_job(C.Structure):
     _fields_ = [("eyes", hrr_eyes), ("n_eyes", C.c_uint32), ("tree", C.c_void_p),
                 ("dev_tile", C.c_void_p), ("tile_w", C.c_uint32), ("tile_h", C.c_uint32),
-                ("tau", C.c_float), ("shift_offset", C.c_uint32), ("cap", C.c_uint64)]
+                ("tau", C.c_float), ("shift_offset", C.c_uint32), ("cap", C.c_uint64),
+                ("tile_d", C.c_uint32), ("sample_index", C.c_uint32)]
 
 
 class hrr_job_result(C.Structure):
@@ -84,7 +86,8 @@ class hrr_server_info(C.Structure):
 
 class hrr_cull_opts(C.Structure):
     _fields_ = [("eye_visits", C.c_void_p), ("rangemin_variant", C.c_int),
-                ("shift_offset", C.c_uint32), ("blocks_per_sm", C.c_uint32)]
+                ("shift_offset", C.c_uint32), ("blocks_per_sm", C.c_uint32),
+                ("sample_index", C.c_uint32)]
 
 
 class hrr_tuning(C.Structure):
@@ -116,6 +119,7 @@ _SIGS = {
     "hrr_tree_info": (_i32, [_P, C.POINTER(_u32), C.POINTER(_u32), C.POINTER(_P)]),
     "hrr_tree_download": (_i32, [_P, _P, _P, _P]),
     "hrr_set_shift_tile": (_i32, [_P, _P, _u32, _u32]),
+    "hrr_set_shift_tile_3d": (_i32, [_P, _P, _u32, _u32, _u32]),
     "hrr_cull": (_i32, [_P, hrr_eyes, _u32, _P, _f32, _P, _u64, C.POINTER(_u64)]),
     "hrr_cull_ex": (_i32, [_P, hrr_eyes, _u32, _P, _f32, C.POINTER(hrr_cull_opts), _P, _u64,
                            C.POINTER(_u64)]),
@@ -164,6 +168,15 @@ def _ptr(t):
     return t.ctypes.data
 
 
+def _tile_dims(tile):
+    """(d, h, w) of a device tile tensor of shape (h, w) or (d, h, w); zeros for None."""
+    if tile is None:
+        return 0, 0, 0
+    if tile.dim() == 3:
+        return int(tile.shape[0]), int(tile.shape[1]), int(tile.shape[2])
+    return 1, int(tile.shape[0]), int(tile.shape[1])
+
+
 class Context:
     """A library context bound to a CUDA device and stream (PyTorch's current stream by
     default). Methods take PyTorch CUDA tensors and return library handles / counts."""
@@ -197,9 +210,15 @@ class Context:
 
     # -- shifts ----------------------------------------------------------------------------
     def set_shift_tile(self, tile: np.ndarray):
+        """A (h, w) tile of shifts, or a (d, h, w) space-time tile (layer n mod d for
+        sample index n)."""
         tile = np.ascontiguousarray(tile, dtype=np.uint32)
-        h, w = tile.shape
-        self.check(hrr_set_shift_tile(self.handle, tile.ctypes.data, w, h))
+        if tile.ndim == 3:
+            d, h, w = tile.shape
+            self.check(hrr_set_shift_tile_3d(self.handle, tile.ctypes.data, w, h, d))
+        else:
+            h, w = tile.shape
+            self.check(hrr_set_shift_tile(self.handle, tile.ctypes.data, w, h))
 
     # -- hierarchy -------------------------------------------------------------------------
     def build_light_tree(self, x, y, z, intensity) -> "Tree":
@@ -211,7 +230,7 @@ class Context:
 
     # -- culling ---------------------------------------------------------------------------
     def cull(self, x, y, z, px, py, tree: "Tree", tau: float, pairs, eye_visits=None,
-             rangemin_variant: int = 0, shift_offset: int = 0, tuning=None):
+             rangemin_variant: int = 0, shift_offset: int = 0, tuning=None, sample_index: int = 0):
         """Cull into ``pairs`` (uint32/int32 tensor of shape (cap, 2)); returns
         (status, count). HRR_ERR_OVERFLOW is returned, not raised. ``tuning`` (a dict as
         returned by autotune) sets the launch shape and overrides rangemin_variant."""
@@ -221,7 +240,7 @@ class Context:
         cnt = _u64()
         t = tuning or {}
         opts = hrr_cull_opts(_ptr(eye_visits), int(t.get("rangemin_variant", rangemin_variant)),
-                             shift_offset, int(t.get("blocks_per_sm", 0)))
+                             shift_offset, int(t.get("blocks_per_sm", 0)), int(sample_index))
         st = hrr_cull_ex(self.handle, E, n, tree.handle, float(tau), C.byref(opts),
                          _ptr(pairs) if cap else None, cap, C.byref(cnt))
         if st not in (HRR_OK, HRR_ERR_OVERFLOW):
@@ -266,7 +285,8 @@ class Batch:
 
     ``frames`` is a list of dicts with keys: x, y, z, px, py (CUDA tensors of one frame's
     eyes), tree (Tree), tau, pairs (int32 tensor (cap, 2)); optional tile (uint32 tensor
-    (h, w) on the device), shift_offset, eye_visits (int32 tensor)."""
+    (h, w) or (d, h, w) on the device), sample_index, shift_offset, eye_visits (int32
+    tensor)."""
 
     def __init__(self, ctx: "Context", frames, rangemin_variant: int = 0, use_graph: bool = True,
                  tuning=None):
@@ -276,14 +296,13 @@ class Batch:
         self._keep = frames  # the frames' tensors must outlive the batch
         for i, fr in enumerate(frames):
             tile = fr.get("tile")
+            d, h, w = _tile_dims(tile)
             arr[i] = hrr_frame(
                 hrr_eyes(_ptr(fr["x"]), _ptr(fr["y"]), _ptr(fr["z"]), _ptr(fr["px"]), _ptr(fr["py"])),
-                int(fr["x"].numel()), fr["tree"].handle,
-                _ptr(tile), int(tile.shape[1]) if tile is not None else 0,
-                int(tile.shape[0]) if tile is not None else 0,
+                int(fr["x"].numel()), fr["tree"].handle, _ptr(tile), w, h,
                 float(fr["tau"]), int(fr.get("shift_offset", 0)),
                 _ptr(fr["pairs"]) if fr["pairs"].shape[0] else None, int(fr["pairs"].shape[0]),
-                _ptr(fr.get("eye_visits")))
+                _ptr(fr.get("eye_visits")), d, int(fr.get("sample_index", 0)))
         h = _P()
         tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0)
         ctx.check(hrr_batch_create(ctx.handle, arr, self.n, C.byref(tn), 1 if use_graph else 0,
@@ -332,11 +351,11 @@ class Server:
         self._keep = {}
 
     def submit(self, x, y, z, px, py, tree: "Tree", tau: float, cap: int, tile=None,
-               shift_offset: int = 0) -> int:
+               shift_offset: int = 0, sample_index: int = 0) -> int:
+        d, h, w = _tile_dims(tile)
         job = hrr_job(hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py)), int(x.numel()),
-                      tree.handle, _ptr(tile), int(tile.shape[1]) if tile is not None else 0,
-                      int(tile.shape[0]) if tile is not None else 0, float(tau), int(shift_offset),
-                      int(cap))
+                      tree.handle, _ptr(tile), w, h, float(tau), int(shift_offset), int(cap), d,
+                      int(sample_index))
         t = _u64()
         self.ctx.check(hrr_server_submit(self.handle, self.ctx.handle, C.byref(job), C.byref(t)))
         self._keep[int(t.value)] = (x, y, z, px, py, tile)

@@ -190,12 +190,13 @@ int hrr_tree_download(hrr_ctx *ctx, const hrr_tree *tree, hrr_node *host_nodes,
     return HRR_OK;
 }
 
-int hrr_set_shift_tile(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, uint32_t h) {
+int hrr_set_shift_tile_3d(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, uint32_t h, uint32_t d) {
     if (!ctx) return HRR_ERR_INVALID_ARG;
-    if (!host_tile || w == 0 || h == 0 || w > 65536 || h > 65536)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tile must be non-empty, at most 65536 x 65536");
+    if (!host_tile || w == 0 || h == 0 || d == 0 || w > 65536 || h > 65536 || d > 65536 ||
+        (uint64_t)w * h * d > (1ull << 30))
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tile must be non-empty, w, h, d <= 65536, w*h*d <= 2^30");
     DeviceGuard g(ctx->device);
-    const size_t bytes = sizeof(uint32_t) * (size_t)w * h;
+    const size_t bytes = sizeof(uint32_t) * (size_t)w * h * d;
     uint32_t *dev = nullptr;
     HRR_CUDA(ctx, cudaMallocAsync(&dev, bytes, ctx->stream));
     cudaError_t e = cudaMemcpyAsync(dev, host_tile, bytes, cudaMemcpyHostToDevice, ctx->stream);
@@ -208,7 +209,12 @@ int hrr_set_shift_tile(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, uint
     ctx->tile = dev;
     ctx->tile_w = w;
     ctx->tile_h = h;
+    ctx->tile_d = d;
     return HRR_OK;
+}
+
+int hrr_set_shift_tile(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, uint32_t h) {
+    return hrr_set_shift_tile_3d(ctx, host_tile, w, h, 1);
 }
 
 int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,

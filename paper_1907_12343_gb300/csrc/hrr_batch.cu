@@ -90,7 +90,8 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
             bad = "a frame's eye array is NULL";
         else if (fr.cap && !fr.dev_pairs) bad = "a frame's dev_pairs is NULL";
         else if (((uintptr_t)fr.dev_pairs & 7u) != 0) bad = "a frame's dev_pairs is not 8-byte aligned";
-        else if (fr.dev_tile && (fr.tile_w == 0 || fr.tile_h == 0 || fr.tile_w > 65536 || fr.tile_h > 65536))
+        else if (fr.dev_tile && (fr.tile_w == 0 || fr.tile_h == 0 || fr.tile_w > 65536 || fr.tile_h > 65536 ||
+                                 fr.tile_d > 65536))
             bad = "a frame's tile size is invalid";
         else if (!fr.dev_tile && !ctx->tile) {
             bad = "a frame has no tile and no context tile is set";
@@ -111,7 +112,8 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
         d.ex = fr.eyes.x; d.ey = fr.eyes.y; d.ez = fr.eyes.z; d.px = fr.eyes.px; d.py = fr.eyes.py;
         d.nodes = reinterpret_cast<const float4 *>(fr.tree->nodes);
         d.perm = fr.tree->perm;
-        d.tile = fr.dev_tile ? fr.dev_tile : ctx->tile;
+        d.tile = fr.dev_tile ? hrr_tile_layer(fr.dev_tile, fr.tile_w, fr.tile_h, fr.tile_d, fr.sample_index)
+                             : hrr_tile_layer(ctx->tile, ctx->tile_w, ctx->tile_h, ctx->tile_d, fr.sample_index);
         d.tile_w = fr.dev_tile ? fr.tile_w : ctx->tile_w;
         d.tile_h = fr.dev_tile ? fr.tile_h : ctx->tile_h;
         d.pairs = reinterpret_cast<uint2 *>(fr.dev_pairs);

@@ -414,7 +414,7 @@ int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tr
         fr.ex = E.x; fr.ey = E.y; fr.ez = E.z; fr.px = E.px; fr.py = E.py;
         fr.nodes = reinterpret_cast<const float4 *>(tree->nodes);
         fr.perm = tree->perm;
-        fr.tile = ctx->tile;
+        fr.tile = hrr_tile_layer(ctx->tile, ctx->tile_w, ctx->tile_h, ctx->tile_d, opts.sample_index);
         fr.pairs = reinterpret_cast<uint2 *>(pairs);
         fr.cap = cap;
         fr.counts = ctx->counters;  // [0] accepted, [1] visits

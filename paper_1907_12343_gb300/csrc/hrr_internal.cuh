@@ -19,7 +19,7 @@ struct hrr_ctx {
     bool own_stream = false;
     // shift tile (library-owned copy)
     uint32_t *tile = nullptr;
-    uint32_t tile_w = 0, tile_h = 0;
+    uint32_t tile_w = 0, tile_h = 0, tile_d = 1;  // d layers of w x h (a space-time tile)
     // device counters of the last cull: [0] accepted pairs, [1] node visits, [2] flags,
     // [3] work cursor
     unsigned long long *counters = nullptr;
@@ -44,6 +44,12 @@ struct hrr_tree {
     hrr_node *nodes = nullptr;  // n - 1 records (one record with the single leaf if n == 1)
     uint32_t *perm = nullptr;   // n
 };
+
+// Layer (sample mod d) of a w x h x d tile: the shifts one culling pass uses.
+inline const uint32_t *hrr_tile_layer(const uint32_t *tile, uint32_t w, uint32_t h, uint32_t d,
+                                      uint32_t sample) {
+    return tile + (size_t)(sample % (d ? d : 1u)) * w * h;
+}
 
 // Status helpers (hrr_abi.cu)
 int hrr_fail(hrr_ctx *ctx, int status, const std::string &msg);
@@ -340,6 +346,14 @@ __device__ __forceinline__ bool hrr_leaf_accepts(uint32_t xi, float tau, float l
     return xi < __float2uint_ru(__fmul_rn(p, 4294967296.0f));
 }
 
+// max(a, b, c) in one instruction (three-operand max of sm_100 and later; a NaN operand
+// is ignored as in fmaxf). Exact, so the same as fmaxf(a, fmaxf(b, c)).
+__device__ __forceinline__ float hrr_max3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // Conservative cull test of a node with box [lo, hi] and maximum intensity imax.
 // den = max(RD gap^2 sum, 1e-4) is at most the float32 max(d2, 1e-4) of any light in the
 // box; rhs = RU(RU(tau max(imax, 0)) (1 + 2^-23)) bounds num_i (1 + 2^-24) from above for
@@ -350,9 +364,9 @@ __device__ __forceinline__ void hrr_node_bound(float tau, float lox, float loy, 
                                                float hix, float hiy, float hiz, float imax,
                                                float ex, float ey, float ez, float &den,
                                                float &rhs) {
-    const float gx = fmaxf(0.0f, fmaxf(__fsub_rd(lox, ex), __fsub_rd(ex, hix)));
-    const float gy = fmaxf(0.0f, fmaxf(__fsub_rd(loy, ey), __fsub_rd(ey, hiy)));
-    const float gz = fmaxf(0.0f, fmaxf(__fsub_rd(loz, ez), __fsub_rd(ez, hiz)));
+    const float gx = hrr_max3(0.0f, __fsub_rd(lox, ex), __fsub_rd(ex, hix));
+    const float gy = hrr_max3(0.0f, __fsub_rd(loy, ey), __fsub_rd(ey, hiy));
+    const float gz = hrr_max3(0.0f, __fsub_rd(loz, ez), __fsub_rd(ez, hiz));
     float d2 = __fmul_rd(gx, gx);
     d2 = __fadd_rd(d2, __fmul_rd(gy, gy));
     d2 = __fadd_rd(d2, __fmul_rd(gz, gz));

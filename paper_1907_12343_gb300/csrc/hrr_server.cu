@@ -417,9 +417,12 @@ int hrr_server_submit(hrr_server *s, hrr_ctx *ctx, const hrr_job *job, uint64_t 
     uint32_t tw = d.tile_w, th = d.tile_h;
     if (!tile) {
         if (!ctx || !ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "job has no tile and no context tile is set");
-        tile = ctx->tile; tw = ctx->tile_w; th = ctx->tile_h;
-    } else if (tw == 0 || th == 0 || tw > 65536 || th > 65536) {
+        tile = hrr_tile_layer(ctx->tile, ctx->tile_w, ctx->tile_h, ctx->tile_d, d.sample_index);
+        tw = ctx->tile_w; th = ctx->tile_h;
+    } else if (tw == 0 || th == 0 || tw > 65536 || th > 65536 || d.tile_d > 65536) {
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job tile size is invalid");
+    } else {
+        tile = hrr_tile_layer(tile, tw, th, d.tile_d, d.sample_index);
     }
     Job *j = new (std::nothrow) Job();
     if (!j) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of a job");

@@ -174,6 +174,30 @@ def shift_tile(w: int, h: int, seed: int) -> np.ndarray:
     return r.astype(np.uint32).reshape(h, w)
 
 
+def shift_tile_3d(w: int, h: int, d: int, seed: int) -> np.ndarray:
+    """uint32 space-time shifts psi(j, n), shape (d, h, w): layer n of pixel p holds
+    ((n + o(p)) mod d + (R(p) + u) / (w h)) / d in 32-bit fixed point.
+
+    R is a void-and-cluster rank tile (blue noise in space) and o(p) in [0, d) the
+    d-level quantisation of a second, independent rank tile; u is seeded uniform dither.
+    Every pixel's d values fall in d distinct strata of [0, 1) (stratified in time), and
+    every layer holds each stratum w h / d times. Requires d to divide w h.
+    """
+    n = w * h
+    if d < 1 or n % d:
+        raise ValueError("shift_tile_3d needs 1 <= d dividing w*h")
+    rank = void_and_cluster(w, h, seed).astype(np.float64).ravel()
+    off = (void_and_cluster(w, h, seed + 1).astype(np.int64).ravel() * d) // n
+    u = uniform01(seed, 0x3D, n)
+    fine = (rank + u) / n
+    out = np.empty((d, n), dtype=np.uint32)
+    for layer in range(d):
+        stratum = (layer + off) % d
+        v = (stratum + fine) / d
+        out[layer] = np.minimum(np.floor(v * 4294967296.0), 4294967295.0).astype(np.uint32)
+    return out.reshape(d, h, w)
+
+
 # --------------------------------------------------------------------------------------
 # Culling scale
 # --------------------------------------------------------------------------------------
