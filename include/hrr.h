@@ -152,6 +152,14 @@ int hrr_kernel_time(hrr_ctx *ctx, double *ms, uint64_t *launches);
  * 1 <= n_lights <= 2^31 - 1. Synchronises the context stream; returns
  * HRR_ERR_INVALID_ARG if any position or intensity is not finite. */
 int hrr_build_light_tree(hrr_ctx *ctx, hrr_lights lights, uint32_t n_lights, hrr_tree **out);
+
+/* Moved lights (the same lights, new positions and intensities; device SoA of the tree's
+ * n lights, indexed by original light id): refit `tree` in place. The leaf order and the
+ * topology of the build stay, so a light keeps its sequence index i (its position in the
+ * build's Morton order, Sec. 1) and culling equals flat culling over that order; the boxes
+ * and maximum intensities are recomputed. Synchronous. HRR_ERR_INVALID_ARG if a value is
+ * not finite (the tree is then unchanged). The tree must not be in use by work in flight. */
+int hrr_refit_light_tree(hrr_ctx *ctx, hrr_tree *tree, hrr_lights lights);
 /* Release a hierarchy (stream-ordered on ctx). */
 int hrr_free_light_tree(hrr_ctx *ctx, hrr_tree *tree);
 /* Device pointer to the sorted-leaf -> original light id permutation (n_lights entries). */
@@ -280,6 +288,13 @@ typedef struct hrr_job {
     uint64_t cap;               /* output pairs to reserve */
     uint32_t tile_d;            /* layers of dev_tile (0 means 1); ignored for the context tile */
     uint32_t sample_index;      /* layer sample_index mod d of the job's tile */
+    /* moved lights for this frame, or all NULL: the server refits `tree` to them (as
+     * hrr_refit_light_tree does) in the job's stream before its first eyes, once every job
+     * submitted earlier that reads the same tree is done; jobs submitted later see the
+     * refitted tree. A light that is not finite fails the job with HRR_ERR_INVALID_ARG and
+     * leaves the tree unchanged. With refit set the server writes `tree` (const above
+     * because other jobs only read it). */
+    hrr_lights refit;
 } hrr_job;
 
 typedef struct hrr_job_result {

@@ -103,6 +103,8 @@ def lib():
             L.or_tree_build.argtypes = [P, P, u32]
             L.or_tree_free.restype = None
             L.or_tree_free.argtypes = [C.POINTER(_Tree)]
+            L.or_tree_refit.restype = None
+            L.or_tree_refit.argtypes = [C.POINTER(_Tree), P, P]
             for nm in ("or_cull_flat", "or_cull_hier"):
                 getattr(L, nm).restype = C.POINTER(_Result)
                 getattr(L, nm).argtypes = [C.POINTER(_Tree), P, P, P, P, u32, P, u32, u32, f32, i32]
@@ -233,6 +235,27 @@ class Tree:
             self.first = self.last = self.split = e32
             self.lo = self.hi = np.zeros((0, 3), dtype=np.float32)
             self.imax = np.zeros(0, dtype=np.float32)
+
+    def _read_boxes(self):
+        t = self._t.contents
+        n, ni = self.n, self.n - 1
+        self.pos = np.ctypeslib.as_array(t.pos, shape=(n * 3,)).reshape(n, 3).copy()
+        self.inten = np.ctypeslib.as_array(t.inten, shape=(n,)).copy()
+        if ni:
+            self.lo = np.ctypeslib.as_array(t.lo, shape=(ni * 3,)).reshape(ni, 3).copy()
+            self.hi = np.ctypeslib.as_array(t.hi, shape=(ni * 3,)).reshape(ni, 3).copy()
+            self.imax = np.ctypeslib.as_array(t.imax, shape=(ni,)).copy()
+
+    def refit(self, light_pos: np.ndarray, intensity: np.ndarray):
+        """Moved lights (same ids): keep the leaf order and topology, recompute the boxes
+        and maximum intensities from the new positions."""
+        pos = np.ascontiguousarray(light_pos, dtype=np.float32).reshape(-1, 3)
+        inten = np.ascontiguousarray(intensity, dtype=np.float32)
+        if len(inten) != self.n or len(pos) != self.n:
+            raise ValueError("refit needs the same number of lights")
+        self._pos, self._inten = pos, inten
+        lib().or_tree_refit(self._t, _ptr(pos), _ptr(inten))
+        self._read_boxes()
 
     def __del__(self):
         t = getattr(self, "_t", None)

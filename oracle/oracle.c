@@ -456,6 +456,27 @@ static int highest_difference(const or_tree *t, uint32_t i, uint32_t j)
     return fls64((uint64_t)(i ^ j));
 }
 
+/* Boxes and maximum intensities of every internal node, straight from the leaves of its
+ * range (the bound the node test of Sec. 1 needs). */
+static void boxes_from_leaves(or_tree *t)
+{
+    uint32_t ni = t->n - 1;
+    for (uint32_t k = 0; k < ni; ++k) {
+        float *lo = &t->lo[3 * k], *hi = &t->hi[3 * k];
+        for (int c = 0; c < 3; ++c)
+            lo[c] = hi[c] = t->pos[3 * t->first[k] + c];
+        float im = t->inten[t->first[k]];
+        for (uint32_t i = t->first[k]; i <= t->last[k]; ++i) {
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = fminf(lo[c], t->pos[3 * i + c]);
+                hi[c] = fmaxf(hi[c], t->pos[3 * i + c]);
+            }
+            im = fmaxf(im, t->inten[i]);
+        }
+        t->imax[k] = im;
+    }
+}
+
 or_tree *or_tree_build(const float *pos, const float *intensity, uint32_t n)
 {
     if (n == 0)
@@ -520,22 +541,20 @@ or_tree *or_tree_build(const float *pos, const float *intensity, uint32_t n)
     }
     free(stack);
 
-    /* Boxes and maximum intensities, straight from the leaves of each range. */
-    for (uint32_t k = 0; k < ni; ++k) {
-        float *lo = &t->lo[3 * k], *hi = &t->hi[3 * k];
-        for (int c = 0; c < 3; ++c)
-            lo[c] = hi[c] = t->pos[3 * t->first[k] + c];
-        float im = t->inten[t->first[k]];
-        for (uint32_t i = t->first[k]; i <= t->last[k]; ++i) {
-            for (int c = 0; c < 3; ++c) {
-                lo[c] = fminf(lo[c], t->pos[3 * i + c]);
-                hi[c] = fmaxf(hi[c], t->pos[3 * i + c]);
-            }
-            im = fmaxf(im, t->inten[i]);
-        }
-        t->imax[k] = im;
-    }
+    boxes_from_leaves(t);
     return t;
+}
+
+void or_tree_refit(or_tree *t, const float *pos, const float *intensity)
+{
+    /* Same leaf order and topology (they came from the build's keys); the leaves take the
+     * new positions and intensities of their original lights. */
+    for (uint32_t i = 0; i < t->n; ++i) {
+        uint32_t id = t->perm[i];
+        memcpy(&t->pos[3 * i], &pos[3 * id], 3 * sizeof(float));
+        t->inten[i] = intensity[id];
+    }
+    boxes_from_leaves(t);
 }
 
 void or_tree_free(or_tree *t)

@@ -73,6 +73,9 @@ typedef struct or_tree {
 
 or_tree *or_tree_build(const float *pos, const float *intensity, uint32_t n);
 void or_tree_free(or_tree *t);
+/* New positions (3 per light) and intensities for the same lights (indexed by original id):
+ * the leaf order and topology stay, boxes and maximum intensities are recomputed. */
+void or_tree_refit(or_tree *t, const float *pos, const float *intensity);
 
 /* ---- culling ---- */
 typedef struct or_cull_result {

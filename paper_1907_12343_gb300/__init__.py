@@ -70,7 +70,7 @@ class hrr_job(C.Structure):
     _fields_ = [("eyes", hrr_eyes), ("n_eyes", C.c_uint32), ("tree", C.c_void_p),
                 ("dev_tile", C.c_void_p), ("tile_w", C.c_uint32), ("tile_h", C.c_uint32),
                 ("tau", C.c_float), ("shift_offset", C.c_uint32), ("cap", C.c_uint64),
-                ("tile_d", C.c_uint32), ("sample_index", C.c_uint32)]
+                ("tile_d", C.c_uint32), ("sample_index", C.c_uint32), ("refit", hrr_lights)]
 
 
 class hrr_job_result(C.Structure):
@@ -120,6 +120,7 @@ _SIGS = {
     "hrr_tree_download": (_i32, [_P, _P, _P, _P]),
     "hrr_set_shift_tile": (_i32, [_P, _P, _u32, _u32]),
     "hrr_set_shift_tile_3d": (_i32, [_P, _P, _u32, _u32, _u32]),
+    "hrr_refit_light_tree": (_i32, [_P, _P, hrr_lights]),
     "hrr_cull": (_i32, [_P, hrr_eyes, _u32, _P, _f32, _P, _u64, C.POINTER(_u64)]),
     "hrr_cull_ex": (_i32, [_P, hrr_eyes, _u32, _P, _f32, C.POINTER(hrr_cull_opts), _P, _u64,
                            C.POINTER(_u64)]),
@@ -227,6 +228,13 @@ class Context:
         t = _P()
         self.check(hrr_build_light_tree(self.handle, L, n, C.byref(t)))
         return Tree(self, t)
+
+    def refit_light_tree(self, tree: "Tree", x, y, z, intensity):
+        """Refit ``tree`` in place to moved lights (same ids, same count)."""
+        if int(x.numel()) != tree.n_lights:
+            raise ValueError("refit needs the tree's light count")
+        self.check(hrr_refit_light_tree(self.handle, tree.handle, hrr_lights(_ptr(x), _ptr(y), _ptr(z),
+                                                                             _ptr(intensity))))
 
     # -- culling ---------------------------------------------------------------------------
     def cull(self, x, y, z, px, py, tree: "Tree", tau: float, pairs, eye_visits=None,
@@ -351,14 +359,17 @@ class Server:
         self._keep = {}
 
     def submit(self, x, y, z, px, py, tree: "Tree", tau: float, cap: int, tile=None,
-               shift_offset: int = 0, sample_index: int = 0) -> int:
+               shift_offset: int = 0, sample_index: int = 0, refit=None) -> int:
+        """Queue a job; ``refit`` = (x, y, z, intensity) device tensors of moved lights refits
+        ``tree`` before the job's eyes (see hrr_job.refit)."""
         d, h, w = _tile_dims(tile)
+        rl = hrr_lights(*(_ptr(a) for a in refit)) if refit is not None else hrr_lights()
         job = hrr_job(hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py)), int(x.numel()),
                       tree.handle, _ptr(tile), w, h, float(tau), int(shift_offset), int(cap), d,
-                      int(sample_index))
+                      int(sample_index), rl)
         t = _u64()
         self.ctx.check(hrr_server_submit(self.handle, self.ctx.handle, C.byref(job), C.byref(t)))
-        self._keep[int(t.value)] = (x, y, z, px, py, tile)
+        self._keep[int(t.value)] = (x, y, z, px, py, tile, refit)
         return int(t.value)
 
     @staticmethod

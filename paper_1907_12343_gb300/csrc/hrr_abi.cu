@@ -190,6 +190,29 @@ int hrr_tree_download(hrr_ctx *ctx, const hrr_tree *tree, hrr_node *host_nodes,
     return HRR_OK;
 }
 
+int hrr_refit_light_tree(hrr_ctx *ctx, hrr_tree *tree, hrr_lights lights) {
+    if (!ctx) return HRR_ERR_INVALID_ARG;
+    if (!tree || tree->device != ctx->device) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tree is NULL or on another device");
+    if (!lights.x || !lights.y || !lights.z || !lights.intensity)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "a light array is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    unsigned long long *flags = ctx->counters + 2;
+    HRR_CUDA(ctx, cudaMemsetAsync(flags, 0, sizeof(unsigned long long), st));
+    void *scratch = nullptr;
+    HRR_CUDA(ctx, cudaMallocAsync(&scratch, hrr_refit_scratch_bytes(tree->n), st));
+    const cudaError_t e = hrr_refit_enqueue(tree, lights, scratch, flags, st);
+    ctx->launches += tree->n > 1 ? 3 : 1;
+    cudaFreeAsync(scratch, st);
+    HRR_CUDA(ctx, e);
+    HRR_CUDA(ctx, cudaMemcpyAsync(&ctx->host_counters[2], flags, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    HRR_CUDA(ctx, cudaStreamSynchronize(st));
+    if (ctx->host_counters[2] & HRR_FLAG_NONFINITE)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "a light position or intensity is not finite");
+    if (ctx->host_counters[2] & HRR_FLAG_TOPOLOGY) return hrr_fail(ctx, HRR_ERR_DEVICE, "inconsistent tree records");
+    return HRR_OK;
+}
+
 int hrr_set_shift_tile_3d(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, uint32_t h, uint32_t d) {
     if (!ctx) return HRR_ERR_INVALID_ARG;
     if (!host_tile || w == 0 || h == 0 || d == 0 || w > 65536 || h > 65536 || d > 65536 ||

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kThreads) refit_kernel(const float4 *__restric
                                                          uint32_t *root_height,
                                                          unsigned long long *flags) {
     const uint32_t leaf = blockIdx.x * kThreads + threadIdx.x;
-    if (leaf >= n) return;
+    if (leaf >= n || (*(volatile unsigned long long *)flags & HRR_FLAG_NONFINITE)) return;
     const float4 p = spos[leaf];
     float lo[3] = {p.x, p.y, p.z}, hi[3] = {p.x, p.y, p.z};
     float imax = p.w;
@@ -241,11 +241,50 @@ __global__ void __launch_bounds__(kThreads) refit_kernel(const float4 *__restric
     }
 }
 
+// Refit for moved lights: the leaves keep their order, so gather the new positions into
+// that order (flagging non-finite values), rebuild the parent links from the records, and
+// run refit_kernel again. The last two skip their work when the gather raised a flag, so
+// the hierarchy is left as it was.
+__global__ void __launch_bounds__(kThreads) gather_check_kernel(const float *__restrict__ x,
+                                                                const float *__restrict__ y,
+                                                                const float *__restrict__ z,
+                                                                const float *__restrict__ inten,
+                                                                const uint32_t *__restrict__ perm,
+                                                                uint32_t n, float4 *__restrict__ spos,
+                                                                unsigned long long *flags) {
+    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t v = perm[i];
+    const float4 p = make_float4(x[v], y[v], z[v], inten[v]);
+    if (!isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z) || !isfinite(p.w)) atomicOr(flags, HRR_FLAG_NONFINITE);
+    spos[i] = p;
+}
+
+__global__ void __launch_bounds__(kThreads) links_kernel(const hrr_node *__restrict__ nodes, uint32_t n,
+                                                         uint32_t *__restrict__ leaf_parent,
+                                                         uint32_t *__restrict__ int_parent,
+                                                         unsigned long long *flags) {
+    const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+    if (i >= n - 1 || (*(volatile unsigned long long *)flags & HRR_FLAG_NONFINITE)) return;
+    const uint32_t s = nodes[i].split, j = nodes[i].other_end;
+    const uint32_t first = min(i, j), last = max(i, j);
+    if (last >= n || s < first || s >= last) {
+        atomicOr(flags, HRR_FLAG_TOPOLOGY);
+        return;
+    }
+    const uint32_t code = i << 1;
+    if (first == s) leaf_parent[s] = code; else int_parent[s] = code;
+    if (last == s + 1) leaf_parent[s + 1] = code | 1u; else int_parent[s + 1] = code | 1u;
+}
+
 __global__ void single_leaf_kernel(const float *x, const float *y, const float *z,
                                    const float *inten, hrr_node *node, uint32_t *perm,
                                    unsigned long long *flags) {
     const float px = x[0], py = y[0], pz = z[0], w = inten[0];
-    if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !isfinite(w)) atomicOr(flags, HRR_FLAG_NONFINITE);
+    if (!isfinite(px) || !isfinite(py) || !isfinite(pz) || !isfinite(w)) {
+        atomicOr(flags, HRR_FLAG_NONFINITE);
+        return;  // a build fails; a refit leaves the record as it was
+    }
     const float lo[3] = {px, py, pz};
     store_slot(node, 0, lo, lo, w);
     store_slot(node, 1, lo, lo, w);
@@ -352,6 +391,43 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
         return fail(hrr_fail(ctx, HRR_ERR_DEVICE, "inconsistent radix-tree links"));
     *out = tree;
     return HRR_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Refit for moved lights
+// ------------------------------------------------------------------------------------
+
+size_t hrr_refit_scratch_bytes(uint32_t n) {
+    const size_t un = (size_t)n;
+    return ((sizeof(float4) * un + 255) & ~size_t(255)) + 2 * ((sizeof(uint32_t) * un + 255) & ~size_t(255)) +
+           ((sizeof(uint32_t) * un + 255) & ~size_t(255)) + ((sizeof(uint32_t) * 2 * un + 255) & ~size_t(255)) +
+           256 + 1024;
+}
+
+cudaError_t hrr_refit_enqueue(hrr_tree *tree, const hrr_lights &L, void *scratch_mem, unsigned long long *flags,
+                              cudaStream_t st) {
+    const uint32_t n = tree->n;
+    if (n == 1) {
+        // one leaf: rewrite the single record unless the light is not finite (checked there)
+        single_leaf_kernel<<<1, 1, 0, st>>>(L.x, L.y, L.z, L.intensity, tree->nodes, tree->perm, flags);
+        return cudaGetLastError();
+    }
+    char *p = static_cast<char *>(scratch_mem);
+    float4 *spos = carve<float4>(p, n);
+    uint32_t *leaf_parent = carve<uint32_t>(p, n), *int_parent = carve<uint32_t>(p, n);
+    uint32_t *arrivals = carve<uint32_t>(p, n);
+    uint32_t *child_height = carve<uint32_t>(p, 2 * (size_t)n);
+    uint32_t *root_height = carve<uint32_t>(p, 1);
+    const unsigned g = (n + kThreads - 1) / kThreads, gi = (n - 1 + kThreads - 1) / kThreads;
+    gather_check_kernel<<<g, kThreads, 0, st>>>(L.x, L.y, L.z, L.intensity, tree->perm, n, spos, flags);
+    cudaError_t e = cudaMemsetAsync(arrivals, 0, sizeof(uint32_t) * (size_t)n, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(leaf_parent, 0xFF, 2 * ((sizeof(uint32_t) * (size_t)n + 255) & ~size_t(255)), st);
+    if (e != cudaSuccess) return e;
+    links_kernel<<<gi, kThreads, 0, st>>>(tree->nodes, n, leaf_parent, int_parent, flags);
+    refit_kernel<<<g, kThreads, 0, st>>>(spos, n, tree->nodes, leaf_parent, int_parent, arrivals, child_height,
+                                         root_height, flags);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------

@@ -129,6 +129,13 @@ cudaError_t hrr_cull_batch_enqueue(unsigned grid, const hrr_cull_frame_t *frames
 void hrr_timing_begin(hrr_ctx *ctx);
 void hrr_timing_end(hrr_ctx *ctx);
 
+// Refit of a hierarchy for moved lights (hrr_build.cu): scratch of
+// hrr_refit_scratch_bytes(tree->n) bytes (256-byte aligned); *flags must be zero and gets
+// HRR_FLAG_NONFINITE (the hierarchy is then left unchanged) or HRR_FLAG_TOPOLOGY.
+size_t hrr_refit_scratch_bytes(uint32_t n);
+cudaError_t hrr_refit_enqueue(hrr_tree *tree, const hrr_lights &lights, void *scratch, unsigned long long *flags,
+                              cudaStream_t st);
+
 // Entry points implemented per translation unit
 int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &lights, uint32_t n, hrr_tree **out);
 int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &eyes, uint32_t n_eyes, const hrr_tree *tree,

@@ -34,6 +34,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kRing = 2;  // slices enqueued at once (one running, one waiting)
+constexpr size_t kSlotWords = 3;  // device counters per job slot: accepted, visits, flags
 
 struct Job {
     uint64_t ticket = 0;
@@ -64,8 +65,8 @@ struct hrr_server {
     int last_slice = -1;                        // ring entry of the most recent slice
     uint64_t budget = 0, used = 0;
     uint32_t slice_eyes = 0, max_slots = 0;
-    unsigned long long *dev_counts = nullptr;   // 2 per slot: accepted, visits
-    unsigned long long *host_counts = nullptr;  // pinned copies, 2 per slot
+    unsigned long long *dev_counts = nullptr;   // kSlotWords per slot: accepted, visits, job flags
+    unsigned long long *host_counts = nullptr;  // pinned copies
     std::vector<hrr_cull_frame_t> host_frames[kRing];  // slice descriptors (kernel parameters)
     unsigned long long *dev_misc = nullptr;     // 2 per ring entry: cursor, flags
     unsigned grid_max = 1;                      // blocks of a full slice's traversal
@@ -108,9 +109,14 @@ void reap(hrr_server *s) {
     for (size_t i = 0; i < s->active.size();) {
         Job *j = s->active[i];
         if (j->all_launched && cudaEventQuery(j->done_ev) == cudaSuccess) {
-            j->count = s->host_counts[2 * (size_t)j->slot];
-            j->visits = s->host_counts[2 * (size_t)j->slot + 1];
-            if (j->status == HRR_PENDING) j->status = j->count > j->desc.cap ? HRR_ERR_OVERFLOW : HRR_OK;
+            const unsigned long long *c = s->host_counts + kSlotWords * (size_t)j->slot;
+            j->count = c[0];
+            j->visits = c[1];
+            if (j->status == HRR_PENDING) {
+                if (c[2] & HRR_FLAG_NONFINITE) j->status = HRR_ERR_INVALID_ARG;  // refit lights
+                else if (c[2] & HRR_FLAG_TOPOLOGY) j->status = HRR_ERR_DEVICE;
+                else j->status = j->count > j->desc.cap ? HRR_ERR_OVERFLOW : HRR_OK;
+            }
             j->t_done = Clock::now();
             j->done = true;
             s->free_slots.push_back(j->slot);
@@ -196,6 +202,16 @@ bool enqueue_slice(hrr_server *s, int k) {
     for (Job *j : s->active) {
         if (j->all_launched) continue;
         if (budget == 0 || work.size() == HRR_CULL_MAX_FRAMES) break;
+        const bool refit = j->next_eye == 0 && j->desc.refit.x != nullptr;
+        if (refit) {
+            // The refit changes the tree under every later reader: it starts a slice in
+            // which no earlier job reads that tree, after everything in flight.
+            bool shared = false;
+            for (Job *w : work) shared |= w->desc.tree == j->desc.tree;
+            if (shared) break;
+            for (int o = 0; o < kRing; ++o)
+                if (o != k && s->slice_busy[o]) cudaStreamWaitEvent(st, s->slice_done[o], 0);
+        }
         if (j->next_eye == 0) {  // first slice of the job: its buffer and counters
             void *p = nullptr;
             if (j->bytes && cudaMallocFromPoolAsync(&p, j->bytes, s->pool, st) != cudaSuccess) {
@@ -203,7 +219,20 @@ bool enqueue_slice(hrr_server *s, int k) {
                 j->status = HRR_ERR_OOM;  // completes (with no pairs) like any other job
             }
             j->pairs = static_cast<uint2 *>(p);
-            cudaMemsetAsync(s->dev_counts + 2 * (size_t)j->slot, 0, 2 * sizeof(unsigned long long), st);
+            unsigned long long *c = s->dev_counts + kSlotWords * (size_t)j->slot;
+            cudaMemsetAsync(c, 0, kSlotWords * sizeof(unsigned long long), st);
+        }
+        if (refit) {  // moved lights: the step before the traversal, in the job's stream
+            void *scratch = nullptr;
+            if (cudaMallocFromPoolAsync(&scratch, hrr_refit_scratch_bytes(j->desc.tree->n), s->pool, st) != cudaSuccess) {
+                cudaGetLastError();
+                j->status = HRR_ERR_OOM;
+            } else {
+                if (hrr_refit_enqueue(const_cast<hrr_tree *>(j->desc.tree), j->desc.refit, scratch,
+                                      s->dev_counts + kSlotWords * (size_t)j->slot + 2, st) == cudaSuccess)
+                    s->launches += j->desc.tree->n > 1 ? 3 : 1;
+                cudaFreeAsync(scratch, st);
+            }
         }
         const uint32_t take = (uint32_t)std::min<uint64_t>(budget, j->desc.n_eyes - j->next_eye);
         work.push_back(j);
@@ -230,7 +259,7 @@ bool enqueue_slice(hrr_server *s, int k) {
         d.tile = j->tile; d.tile_w = j->tile_w; d.tile_h = j->tile_h;
         d.pairs = j->pairs;
         d.cap = j->pairs ? j->desc.cap : 0;  // no buffer (allocation failed): count only
-        d.counts = s->dev_counts + 2 * (size_t)j->slot;
+        d.counts = s->dev_counts + kSlotWords * (size_t)j->slot;
         d.eye_visits = nullptr;
         d.n_lights = j->desc.tree->n;
         d.shift_offset = j->desc.shift_offset;
@@ -258,8 +287,8 @@ bool enqueue_slice(hrr_server *s, int k) {
         // its results are complete only after both
         cudaStreamWaitEvent(st, s->slice_done[s->last_slice], 0);
     for (Job *j : finishing) {
-        cudaMemcpyAsync(s->host_counts + 2 * (size_t)j->slot, s->dev_counts + 2 * (size_t)j->slot,
-                        2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(s->host_counts + kSlotWords * (size_t)j->slot, s->dev_counts + kSlotWords * (size_t)j->slot,
+                        kSlotWords * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
         cudaEventRecord(j->done_ev, st);
         j->all_launched = true;
     }
@@ -366,8 +395,8 @@ int hrr_server_create(hrr_ctx *ctx, uint64_t hbm_budget_bytes, uint32_t slice_ey
     s->slice_stream[0] = s->stream;
     for (int k = 1; k < kRing && e == cudaSuccess; ++k)
         e = cudaStreamCreateWithFlags(&s->slice_stream[k], cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&s->dev_counts, sizeof(unsigned long long) * 2 * max_jobs);
-    if (e == cudaSuccess) e = cudaMallocHost(&s->host_counts, sizeof(unsigned long long) * 2 * max_jobs);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dev_counts, sizeof(unsigned long long) * kSlotWords * max_jobs);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->host_counts, sizeof(unsigned long long) * kSlotWords * max_jobs);
     if (e == cudaSuccess) e = cudaMalloc(&s->dev_misc, sizeof(unsigned long long) * 2 * kRing);
     if (e == cudaSuccess) e = cudaMallocHost(&s->host_flags, sizeof(unsigned long long) * kRing);
     for (int k = 0; k < kRing && e == cudaSuccess; ++k) {
@@ -413,6 +442,8 @@ int hrr_server_submit(hrr_server *s, hrr_ctx *ctx, const hrr_job *job, uint64_t 
     if (!d.tree || d.tree->device != s->device || !(d.tau >= 0.0f) || !(d.tau < __builtin_huge_valf()) ||
         (d.n_eyes && (!d.eyes.x || !d.eyes.y || !d.eyes.z || !d.eyes.px || !d.eyes.py)))
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job has a NULL or foreign tree, a bad tau or a NULL eye array");
+    if (d.refit.x && (!d.refit.y || !d.refit.z || !d.refit.intensity))
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job refit lights are partly NULL");
     const uint32_t *tile = d.dev_tile;
     uint32_t tw = d.tile_w, th = d.tile_h;
     if (!tile) {
