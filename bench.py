@@ -204,6 +204,8 @@ def run_ours(args):
 
     # end to end through the public API with host buffers
     e2e = None if args.no_e2e else run_e2e(ctx, s, dev, stream, args, cap)
+    # the per-frame hierarchy update for moved lights, against a full build
+    refit = run_refit(ctx, L, dev, stream) if ws == 1 else None
     del pairs, flush
 
     # the batched (64 uneven frames) and served (Poisson jobs) forms, 1 GPU only
@@ -220,6 +222,10 @@ def run_ours(args):
                 cap_jobs = args.batch_frames / (batched["plain_job_by_job"]["ms"] / 1e3)
                 served["sustainable"] = run_served(ctx, frames, stream, dev, max(16, args.served_jobs // 4),
                                                    0.7 * cap_jobs, seed=12, tuning=tn)
+                # and with each job refitting its frame's hierarchy to moved lights first
+                served["sustainable_refit"] = run_served(ctx, frames, stream, dev, max(16, args.served_jobs // 4),
+                                                         0.7 * cap_jobs, seed=12, tuning=tn,
+                                                         refit_sets=moved_light_sets(frames, dev))
         for fr in frames:
             fr["tree"].free()
 
@@ -237,6 +243,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}"},
             "accepted_pairs": int(cnt), "accepted_per_eye": cnt / n_e, "node_visits": int(V),
             "cull_only": {"ms": cull_ms, "value": n_e * n_l / (cull_ms / 1e3), "unit": UNIT},
+            "refit": refit,
             "wall_s": wall,
             "roofline": roof,
             "e2e": e2e,
@@ -260,7 +267,7 @@ def run_ours(args):
 OPS_PER_VISIT = 1.963 * 27 + 0.977 * 51 + 0.774 * 2 + 0.037 * 17
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_1920x1080.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
-                  for f in ("hrr_cull.cu", "hrr_internal.cuh")]
+                  for f in ("hrr_cull.cu", "hrr_math.cuh")]
 
 
 def kernel_source_hash() -> str:
@@ -391,7 +398,7 @@ def upload_frames(ctx, frames_np, dev):
         ep = torch.from_numpy(s.eye_pos).to(dev)
         L = [lp[:, k].contiguous() for k in range(3)] + [torch.from_numpy(s.intensity).to(dev)]
         tree = ctx.build_light_tree(*L)
-        out.append({"x": ep[:, 0].contiguous(), "y": ep[:, 1].contiguous(), "z": ep[:, 2].contiguous(),
+        out.append({"lights": L, "x": ep[:, 0].contiguous(), "y": ep[:, 1].contiguous(), "z": ep[:, 2].contiguous(),
                     "px": torch.from_numpy(s.px.view(np.int16)).to(dev),
                     "py": torch.from_numpy(s.py.view(np.int16)).to(dev),
                     "tree": tree, "tau": float(s.tau), "tile_np": s.tile,
@@ -481,10 +488,65 @@ def _latency_stats(lat):
             "max_s": float(a[-1])}
 
 
+def run_refit(ctx, L, dev, stream, reps=5):
+    """Median device time of hrr_refit_light_tree (moved lights, same ids) and of a full
+    hrr_build_light_tree over the frame's lights."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(17)
+    moved = [torch.clamp(c + (torch.rand(c.shape, generator=gen, device=dev) - 0.5) * 0.04, 0.0, 1.0).contiguous()
+             for c in L[:3]] + [L[3]]
+    tree = ctx.build_light_tree(*L)
+    t_refit, t_build = [], []
+    with torch.cuda.stream(stream):
+        for k in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.refit_light_tree(tree, *(moved if k % 2 == 0 else L))
+            b.record(stream)
+            b.synchronize()
+            if k:
+                t_refit.append(a.elapsed_time(b))
+        for k in range(reps + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            t2 = ctx.build_light_tree(*L)
+            b.record(stream)
+            b.synchronize()
+            t2.free()
+            if k:
+                t_build.append(a.elapsed_time(b))
+    tree.free()
+    return {"n_lights": int(L[0].numel()), "refit_ms": statistics.median(t_refit),
+            "build_ms": statistics.median(t_build)}
+
+
+def moved_light_sets(frames, dev, seed=13, sets=2):
+    """Per frame, `sets` device copies of its lights jittered in position (+-2% of the
+    scene) and intensity (x U[0.5, 1.5]): the lights of later animation frames. Seeded
+    torch generator on the device (timing input only; no result is compared)."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    out = []
+    for fr in frames:
+        x, y, z, inten = fr["lights"]
+        per = []
+        for _ in range(sets):
+            moved = [torch.clamp(c + (torch.rand(c.shape, generator=gen, device=dev) - 0.5) * 0.04, 0.0, 1.0)
+                     for c in (x, y, z)]
+            moved.append(inten * (0.5 + torch.rand(inten.shape, generator=gen, device=dev)))
+            per.append([m.contiguous() for m in moved])
+        out.append(per)
+    return out
+
+
 def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30, slice_eyes=1 << 20,
-               tuning=None):
+               tuning=None, refit_sets=None):
     """Poisson arrivals of frame-sized jobs against resident hierarchies and tiles, served
-    with continuous batching, against the same arrival sequence processed job by job."""
+    with continuous batching, against the same arrival sequence processed job by job. With
+    refit_sets, job k refits its frame's hierarchy to moved lights (set k mod 2) before its
+    eyes, in both forms: the per-frame update before the hot path is part of the latency."""
     import threading as th
     import numpy as np
     import torch
@@ -494,6 +556,9 @@ def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30
     arrive = np.cumsum(gaps) - gaps[0]
     which = np.minimum((synth.uniform01(seed, 51, n_jobs) * len(frames)).astype(int), len(frames) - 1)
     work = sum(frames[f]["n_e"] * frames[f]["n_l"] for f in which)
+    moved = (lambda k: refit_sets[which[k]][k % 2]) if refit_sets is not None else (lambda k: None)
+    # moved lights change the counts: reserve room and check counts only without them
+    cap_of = (lambda fr: 2 * fr["count"] + 4096) if refit_sets is not None else (lambda fr: fr["count"] + 1024)
 
     # served
     srv = hrr.Server(ctx, budget, slice_eyes=slice_eyes, max_jobs=max(64, n_jobs), tuning=tuning)
@@ -507,7 +572,7 @@ def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30
                 time.sleep(dt)
             fr = frames[which[k]]
             tickets[k] = srv.submit(fr["x"], fr["y"], fr["z"], fr["px"], fr["py"], fr["tree"], fr["tau"],
-                                    fr["count"] + 1024, tile=fr["tile"])
+                                    cap_of(fr), tile=fr["tile"], refit=moved(k))
 
     thr = th.Thread(target=submitter)
     thr.start()
@@ -516,7 +581,7 @@ def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30
         while tickets[k] is None:
             time.sleep(0.0005)
         r = srv.wait(tickets[k], 3600.0)
-        if r["status"] != hrr.HRR_OK or r["count"] != frames[which[k]]["count"]:
+        if r["status"] != hrr.HRR_OK or (refit_sets is None and r["count"] != frames[which[k]]["count"]):
             mismatch += 1
         lat.append(r["latency_s"])
         srv.release(tickets[k])
@@ -526,17 +591,20 @@ def run_served(ctx, frames, stream, dev, n_jobs, rate, seed=11, budget=150 << 30
     srv.destroy()
 
     # plain, job by job in arrival order on the same GPU
-    scratch = torch.empty((max(fr["count"] for fr in frames) + 1024, 2), dtype=torch.int32, device=dev)
+    scratch = torch.empty((max(cap_of(fr) for fr in frames), 2), dtype=torch.int32, device=dev)
     lat_p = []
     t0 = time.perf_counter()
     for k in range(n_jobs):
         dt = t0 + arrive[k] - time.perf_counter()
         if dt > 0:
             time.sleep(dt)
+        if refit_sets is not None:
+            ctx.refit_light_tree(frames[which[k]]["tree"], *moved(k))
         plain_frame(ctx, frames[which[k]], scratch, stream, tuning)
         lat_p.append(time.perf_counter() - t0 - arrive[k])
     makespan_p = time.perf_counter() - t0
     return {"jobs": n_jobs, "rate_per_s": rate, "hbm_budget_gb": budget / 2**30, "slice_eyes": slice_eyes,
+            "refit_per_job": refit_sets is not None,
             "value": work / makespan, "unit": UNIT, "latency": _latency_stats(lat),
             "max_active": stats["max_active"], "slices": stats["slices"], "mismatched_jobs": mismatch,
             "plain_job_by_job": {"value": work / makespan_p, "latency": _latency_stats(lat_p)}}

@@ -65,6 +65,7 @@ struct hrr_server {
     int last_slice = -1;                        // ring entry of the most recent slice
     uint64_t budget = 0, used = 0;
     uint32_t slice_eyes = 0, max_slots = 0;
+    uint32_t slice_min_eyes = 1u << 16;         // a slice may end after a finishing job past this
     unsigned long long *dev_counts = nullptr;   // kSlotWords per slot: accepted, visits, job flags
     unsigned long long *host_counts = nullptr;  // pinned copies
     std::vector<hrr_cull_frame_t> host_frames[kRing];  // slice descriptors (kernel parameters)
@@ -238,6 +239,11 @@ bool enqueue_slice(hrr_server *s, int k) {
         work.push_back(j);
         takes.push_back(take);
         budget -= take;
+        // A job completes when its slice does: once a job's last eyes are in, the slice
+        // ends (when it already has enough eyes to fill the GPU), so no job waits for the
+        // eyes of jobs behind it. The next slice, on the other stream, takes over as this
+        // one drains.
+        if (take == j->desc.n_eyes - j->next_eye && s->slice_eyes - budget >= s->slice_min_eyes) break;
     }
     if (work.empty()) return false;
     uint32_t height = 0;
