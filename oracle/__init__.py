@@ -111,6 +111,12 @@ def lib():
             L.or_cull_free.restype = None
             L.or_cull_free.argtypes = [C.POINTER(_Result)]
             L.or_max_threads.restype = i32
+            L.or_pair_weight.restype = None
+            L.or_pair_weight.argtypes = [f32, P, f32, P, P, P]
+            L.or_segment_hits.restype = i32
+            L.or_segment_hits.argtypes = [P, P, P]
+            L.or_connect.restype = None
+            L.or_connect.argtypes = [P, u32, P, P, P, u64, f32, P, u32, P, P, P, i32]
             _lib = L
     return _lib
 
@@ -315,3 +321,39 @@ def cull_hier(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, 
 
 def max_threads() -> int:
     return int(lib().or_max_threads())
+
+
+# ---- connection evaluation ----------------------------------------------------------
+
+def pair_weight(tau, l, intensity, e):
+    """(weight, p) of one accepted connection: (I / max(d^2, 1e-4)) / p in float32."""
+    lv = np.ascontiguousarray(l, dtype=np.float32)
+    ev = np.ascontiguousarray(e, dtype=np.float32)
+    w, p = C.c_float(), C.c_float()
+    lib().or_pair_weight(np.float32(tau), _ptr(lv), np.float32(intensity), _ptr(ev), C.byref(w), C.byref(p))
+    return np.float32(w.value), np.float32(p.value)
+
+
+def segment_hits(e, l, tri) -> bool:
+    """Whether the open segment e -> l crosses the closed triangle (3 x 3 vertices)."""
+    ev = np.ascontiguousarray(e, dtype=np.float32)
+    lv = np.ascontiguousarray(l, dtype=np.float32)
+    tv = np.ascontiguousarray(tri, dtype=np.float32).reshape(9)
+    return bool(lib().or_segment_hits(_ptr(ev), _ptr(lv), _ptr(tv)))
+
+
+def connect(eye_pos, light_pos, intensity, pairs, tau, tris=None, nthreads=0):
+    """Per accepted pair (eye id, light id): weight x visibility (float32), visibility,
+    and per-eye sums (float64). light_pos / intensity are indexed by light id."""
+    eye_pos = np.ascontiguousarray(eye_pos, dtype=np.float32).reshape(-1, 3)
+    light_pos = np.ascontiguousarray(light_pos, dtype=np.float32).reshape(-1, 3)
+    intensity = np.ascontiguousarray(intensity, dtype=np.float32)
+    pairs = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    tris = np.zeros((0, 9), np.float32) if tris is None else np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
+    n = len(pairs)
+    weight = np.zeros(max(n, 1), np.float32)
+    vis = np.zeros(max(n, 1), np.uint8)
+    sums = np.zeros(max(len(eye_pos), 1), np.float64)
+    lib().or_connect(_ptr(eye_pos), len(eye_pos), _ptr(light_pos), _ptr(intensity), _ptr(pairs), n,
+                     np.float32(tau), _ptr(tris), len(tris), _ptr(weight), _ptr(vis), _ptr(sums), nthreads)
+    return {"weight": weight[:n], "visible": vis[:n].astype(bool), "eye_sum": sums[:len(eye_pos)]}

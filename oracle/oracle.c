@@ -756,3 +756,103 @@ void or_cull_free(or_cull_result *res)
     free(res->visits);
     free(res);
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Connection evaluation: the step after the culling                                      */
+/* ------------------------------------------------------------------------------------ */
+
+/* An accepted connection carries the light's unoccluded contribution I / max(d^2, 1e-4)
+ * divided by its acceptance probability p (Russian roulette keeps the sum over accepted
+ * lights an unbiased estimate of the sum over all lights). d^2 and p are the acceptance
+ * rule's own float32 values; every operation rounds to nearest, none is fused. */
+void or_pair_weight(float tau, const float l[3], float intensity, const float e[3], float *weight, float *p_out)
+{
+    float dx = l[0] - e[0];
+    float dy = l[1] - e[1];
+    float dz = l[2] - e[2];
+    float d2 = dx * dx;
+    d2 = d2 + dy * dy;
+    d2 = d2 + dz * dz;
+    float den = fmaxf(d2, kMinDist2);
+    float p = fminf(1.0f, (tau * intensity) / den);
+    float base = intensity / den;
+    *weight = base / p;
+    if (p_out)
+        *p_out = p;
+}
+
+static const float kSegTMin = 1e-4f, kSegTMax = 1.0f - 1e-4f;
+
+/* Does the open segment e + t (l - e), t in (1e-4, 1 - 1e-4), cross the closed triangle
+ * (v0, v1, v2)? Moller-Trumbore: with D = l - e, e1 = v1 - v0, e2 = v2 - v0, P = D x e2,
+ * det = e1 . P, T = e - v0, Q = T x e1, the barycentrics are u = (T . P) / det and
+ * v = (D . Q) / det and the ray parameter t = (e2 . Q) / det. det == 0 (segment parallel
+ * to the plane) is no hit. float32, each product and sum rounded separately, dot products
+ * summed x + y then + z, 1 / det rounded once. */
+int or_segment_hits(const float e[3], const float l[3], const float tri[9])
+{
+    float D[3], e1[3], e2[3], T[3], P[3], Q[3];
+    for (int c = 0; c < 3; ++c) {
+        D[c] = l[c] - e[c];
+        e1[c] = tri[3 + c] - tri[c];
+        e2[c] = tri[6 + c] - tri[c];
+        T[c] = e[c] - tri[c];
+    }
+    P[0] = D[1] * e2[2] - D[2] * e2[1];
+    P[1] = D[2] * e2[0] - D[0] * e2[2];
+    P[2] = D[0] * e2[1] - D[1] * e2[0];
+    float det = e1[0] * P[0];
+    det = det + e1[1] * P[1];
+    det = det + e1[2] * P[2];
+    if (det == 0.0f)
+        return 0;
+    float inv = 1.0f / det;
+    float tp = T[0] * P[0];
+    tp = tp + T[1] * P[1];
+    tp = tp + T[2] * P[2];
+    float u = tp * inv;
+    if (!(u >= 0.0f && u <= 1.0f))
+        return 0;
+    Q[0] = T[1] * e1[2] - T[2] * e1[1];
+    Q[1] = T[2] * e1[0] - T[0] * e1[2];
+    Q[2] = T[0] * e1[1] - T[1] * e1[0];
+    float dq = D[0] * Q[0];
+    dq = dq + D[1] * Q[1];
+    dq = dq + D[2] * Q[2];
+    float v = dq * inv;
+    if (!(v >= 0.0f && u + v <= 1.0f))
+        return 0;
+    float eq = e2[0] * Q[0];
+    eq = eq + e2[1] * Q[1];
+    eq = eq + e2[2] * Q[2];
+    float t = eq * inv;
+    return t > kSegTMin && t < kSegTMax;
+}
+
+/* Weight of every accepted pair (eye id, light id) times its visibility against all
+ * triangles (brute force; n_tri = 0 means nothing occludes), and the per-eye sums in
+ * double precision, added in pair order. */
+void or_connect(const float *eye_pos, uint32_t n_eyes, const float *light_pos, const float *intensity,
+                const uint32_t *pairs, uint64_t n_pairs, float tau, const float *tris, uint32_t n_tri,
+                float *weight, uint8_t *visible, double *eye_sum, int nthreads)
+{
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t k = 0; k < (int64_t)n_pairs; ++k) {
+        uint32_t j = pairs[2 * k], id = pairs[2 * k + 1];
+        const float *e = &eye_pos[3 * (uint64_t)j], *l = &light_pos[3 * (uint64_t)id];
+        float w;
+        or_pair_weight(tau, l, intensity[id], e, &w, NULL);
+        int vis = 1;
+        for (uint32_t q = 0; q < n_tri && vis; ++q)
+            if (or_segment_hits(e, l, &tris[9 * (uint64_t)q]))
+                vis = 0;
+        weight[k] = vis ? w : 0.0f;
+        visible[k] = (uint8_t)vis;
+    }
+    for (uint32_t j = 0; j < n_eyes; ++j)
+        eye_sum[j] = 0.0;
+    for (uint64_t k = 0; k < n_pairs; ++k)
+        eye_sum[pairs[2 * k]] += (double)weight[k];
+}

@@ -103,6 +103,19 @@ void or_cull_free(or_cull_result *res);
 
 int or_max_threads(void);
 
+/* ---- connection evaluation (after the culling) ---- */
+/* weight = (I / max(d^2, 1e-4)) / p of one accepted connection; p the acceptance
+ * probability (p_out may be NULL). */
+void or_pair_weight(float tau, const float l[3], float intensity, const float e[3], float *weight, float *p_out);
+/* 1 iff the open segment e -> l (t in (1e-4, 1 - 1e-4)) crosses the closed triangle
+ * tri = (v0, v1, v2), 9 floats (Moller-Trumbore in float32). */
+int or_segment_hits(const float e[3], const float l[3], const float tri[9]);
+/* Per accepted pair (eye id, light id): weight times visibility against n_tri triangles
+ * (brute force), the visibility bit, and per-eye sums (double, in pair order). */
+void or_connect(const float *eye_pos, uint32_t n_eyes, const float *light_pos, const float *intensity,
+                const uint32_t *pairs, uint64_t n_pairs, float tau, const float *tris, uint32_t n_tri,
+                float *weight, uint8_t *visible, double *eye_sum, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

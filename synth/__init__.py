@@ -198,6 +198,15 @@ def shift_tile_3d(w: int, h: int, d: int, seed: int) -> np.ndarray:
     return out.reshape(d, h, w)
 
 
+def occluder_triangles(n_tri: int, seed: int, size: float = 0.01) -> np.ndarray:
+    """Occluders for the connections' visibility: n_tri small triangles, shape (n_tri, 9)
+    float32 (v0, v1, v2). Centres are uniform in [0, 1)^3; each vertex is the centre plus
+    an isotropic normal offset of standard deviation `size`."""
+    c = uniform01(seed, 0x7A1, 3 * n_tri).reshape(n_tri, 1, 3)
+    off = normal(seed, 0x7A2, 9 * n_tri).reshape(n_tri, 3, 3) * size
+    return (c + off).reshape(n_tri, 9).astype(np.float32)
+
+
 # --------------------------------------------------------------------------------------
 # Culling scale
 # --------------------------------------------------------------------------------------
