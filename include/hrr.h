@@ -356,6 +356,30 @@ int hrr_server_destroy(hrr_server *server);
 int hrr_autotune(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
                  uint32_t *dev_pairs, uint64_t cap, hrr_tuning *best, double *best_ms);
 
+/* ---- connection evaluation (after the culling) --------------------------------------- */
+
+typedef struct hrr_scene hrr_scene; /* opaque, library-owned: a triangle hierarchy */
+
+/* Build a bounding-volume hierarchy over n_tris triangles (device memory, 9 floats each:
+ * v0, v1, v2), copied into the scene. 1 <= n_tris <= 2^31 - 1. Synchronous.
+ * HRR_ERR_INVALID_ARG if a vertex is not finite. */
+int hrr_build_scene(hrr_ctx *ctx, const float *dev_tris, uint32_t n_tris, hrr_scene **out);
+int hrr_free_scene(hrr_ctx *ctx, hrr_scene *scene);
+
+/* Evaluate accepted connections (the step after the culling, Sec. 1): for each of the
+ * n_pairs pairs (eye index, light id) in dev_pairs (as hrr_cull writes them), the
+ * Russian-roulette weight (I / max(d^2, 1e-4)) / p, with d^2 and p the acceptance rule's
+ * float32 values, times the visibility of the open segment eye -> light (t in
+ * (1e-4, 1 - 1e-4)) against the scene's triangles (scene NULL: every connection is
+ * visible). Writes the weights (dev_weight, n_pairs floats, may be NULL), the visibility
+ * bits (dev_visible, n_pairs bytes, may be NULL) and the per-eye sums (dev_eye_sum, n_eyes
+ * floats, zeroed first; float atomics, so the last bits depend on the order). lights are
+ * the SoA indexed by original light id. Synchronous. HRR_ERR_INVALID_ARG if a pair's index
+ * is out of range. */
+int hrr_connect(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, hrr_lights lights, uint32_t n_lights,
+                float tau, const uint32_t *dev_pairs, uint64_t n_pairs, const hrr_scene *scene,
+                float *dev_weight, uint8_t *dev_visible, float *dev_eye_sum);
+
 /* ---- range minimum (Sec. 2, Alg. 1-3) -------------------------------------------------- */
 
 /* For q in [0, n): out_min[q] = min_{i in [a[q], b[q])} (brev32(i) + r[q]) mod 2^32 and

@@ -121,6 +121,9 @@ _SIGS = {
     "hrr_set_shift_tile": (_i32, [_P, _P, _u32, _u32]),
     "hrr_set_shift_tile_3d": (_i32, [_P, _P, _u32, _u32, _u32]),
     "hrr_refit_light_tree": (_i32, [_P, _P, hrr_lights]),
+    "hrr_build_scene": (_i32, [_P, _P, _u32, C.POINTER(_P)]),
+    "hrr_free_scene": (_i32, [_P, _P]),
+    "hrr_connect": (_i32, [_P, hrr_eyes, _u32, hrr_lights, _u32, _f32, _P, _u64, _P, _P, _P, _P]),
     "hrr_cull": (_i32, [_P, hrr_eyes, _u32, _P, _f32, _P, _u64, C.POINTER(_u64)]),
     "hrr_cull_ex": (_i32, [_P, hrr_eyes, _u32, _P, _f32, C.POINTER(hrr_cull_opts), _P, _u64,
                            C.POINTER(_u64)]),
@@ -235,6 +238,23 @@ class Context:
             raise ValueError("refit needs the tree's light count")
         self.check(hrr_refit_light_tree(self.handle, tree.handle, hrr_lights(_ptr(x), _ptr(y), _ptr(z),
                                                                              _ptr(intensity))))
+
+    # -- connection evaluation -------------------------------------------------------------
+    def build_scene(self, tris) -> "Scene":
+        """Triangle hierarchy from a (n, 9) float32 CUDA tensor (v0, v1, v2 per row)."""
+        h = _P()
+        self.check(hrr_build_scene(self.handle, _ptr(tris), int(tris.shape[0]), C.byref(h)))
+        return Scene(self, h)
+
+    def connect(self, x, y, z, lights, tau: float, pairs, n_pairs: int, scene=None, weight=None, visible=None,
+                eye_sum=None):
+        """Weights x visibility of the first n_pairs accepted pairs; lights = (x, y, z,
+        intensity) tensors by light id; eye_sum (float32, one per eye) receives the sums."""
+        E = hrr_eyes(_ptr(x), _ptr(y), _ptr(z), None, None)
+        L = hrr_lights(*(_ptr(a) for a in lights))
+        self.check(hrr_connect(self.handle, E, int(x.numel()), L, int(lights[0].numel()), float(tau), _ptr(pairs),
+                               int(n_pairs), scene.handle if scene is not None else None, _ptr(weight),
+                               _ptr(visible), _ptr(eye_sum)))
 
     # -- culling ---------------------------------------------------------------------------
     def cull(self, x, y, z, px, py, tree: "Tree", tau: float, pairs, eye_visits=None,
@@ -421,6 +441,19 @@ class Server:
             self.destroy()
         except Exception:
             pass
+
+
+class Scene:
+    """A device-resident triangle hierarchy (occluders of the connections)."""
+
+    def __init__(self, ctx: "Context", handle):
+        self.ctx = ctx
+        self.handle = handle
+
+    def free(self):
+        if self.handle:
+            self.ctx.check(hrr_free_scene(self.ctx.handle, self.handle))
+            self.handle = None
 
 
 class Tree:

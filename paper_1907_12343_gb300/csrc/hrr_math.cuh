@@ -10,6 +10,7 @@ enum : unsigned long long {
     HRR_FLAG_STACK = 1ull,     // traversal stack spill area would overflow (not seen for any tree)
     HRR_FLAG_NONFINITE = 2ull, // a light position or intensity is not finite
     HRR_FLAG_TOPOLOGY = 4ull,  // a node record or parent link is out of range
+    HRR_FLAG_RANGE = 8ull,     // an input index (a pair's eye or light) is out of range
 };
 
 // ------------------------------------------------------------------------------------
