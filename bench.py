@@ -206,6 +206,8 @@ def run_ours(args):
     e2e = None if args.no_e2e else run_e2e(ctx, s, dev, stream, args, cap)
     # the per-frame hierarchy update for moved lights, against a full build
     refit = run_refit(ctx, L, dev, stream) if ws == 1 else None
+    # the step after the culling: weights and shadow segments of the accepted pairs
+    connect = run_connect(ctx, E, L, tau, pairs, cnt, dev, stream) if ws == 1 else None
     del pairs, flush
 
     # the batched (64 uneven frames) and served (Poisson jobs) forms, 1 GPU only
@@ -244,6 +246,7 @@ def run_ours(args):
             "accepted_pairs": int(cnt), "accepted_per_eye": cnt / n_e, "node_visits": int(V),
             "cull_only": {"ms": cull_ms, "value": n_e * n_l / (cull_ms / 1e3), "unit": UNIT},
             "refit": refit,
+            "connect": connect,
             "wall_s": wall,
             "roofline": roof,
             "e2e": e2e,
@@ -486,6 +489,45 @@ def _latency_stats(lat):
     a = np.sort(np.asarray(lat))
     return {"p50_s": float(np.percentile(a, 50)), "p99_s": float(np.percentile(a, 99)),
             "max_s": float(a[-1])}
+
+
+def run_connect(ctx, E, L, tau, pairs, n_pairs, dev, stream, n_tris=1 << 18, reps=3):
+    """Connection evaluation of the frame's accepted pairs: Russian-roulette weights alone,
+    and with shadow segments against n_tris seeded occluder triangles (about half the
+    connections blocked). Median device times of hrr_connect; the scene build is timed
+    once."""
+    import torch
+    import synth
+    n_e = int(E[0].numel())
+    tris = torch.from_numpy(synth.occluder_triangles(n_tris, 21, size=0.003)).to(dev)
+    sums = torch.zeros(n_e, dtype=torch.float32, device=dev)
+    vis = torch.zeros(max(int(n_pairs), 1), dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), out
+
+    with torch.cuda.stream(stream):
+        scene_ms, scene = timed(lambda: ctx.build_scene(tris))
+        t_plain, t_vis = [], []
+        for k in range(reps + 1):
+            ms, _ = timed(lambda: ctx.connect(*E, L, tau, pairs, n_pairs, eye_sum=sums))
+            if k:
+                t_plain.append(ms)
+        for k in range(reps + 1):
+            ms, _ = timed(lambda: ctx.connect(*E, L, tau, pairs, n_pairs, scene=scene, visible=vis, eye_sum=sums))
+            if k:
+                t_vis.append(ms)
+        frac = float(vis[:n_pairs].float().mean().item()) if n_pairs else 0.0
+        scene.free()
+    m_plain, m_vis = statistics.median(t_plain), statistics.median(t_vis)
+    return {"pairs": int(n_pairs), "weights_ms": m_plain, "weights_value": n_pairs / (m_plain / 1e3),
+            "occluders": n_tris, "scene_build_ms": scene_ms, "visibility_ms": m_vis,
+            "visibility_value": n_pairs / (m_vis / 1e3), "unit": "connections/s", "visible_fraction": frac}
 
 
 def run_refit(ctx, L, dev, stream, reps=5):
