@@ -200,7 +200,7 @@ def run_ours(args):
     cull_ms = kern_ms / max(kern_n, 1)
     V = statistics.median(visits)
     peaks, kind = _peaks()
-    roof = roofline(V, cnt, n_e, cull_ms, peaks, kind, clk)
+    roof = roofline(V, cnt, n_e, cull_ms, peaks, kind, clk, workload=f"{args.eyes}x{n_l}")
 
     # end to end through the public API with host buffers
     e2e = None if args.no_e2e else run_e2e(ctx, s, dev, stream, args, cap)
@@ -282,9 +282,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(workload=""):
     """DRAM bytes per cull launch from the committed ncu summary, if it was taken on the
-    current kernel source (null otherwise)."""
+    current kernel source and on this workload (null otherwise)."""
     try:
         text = open(PROFILE_SUMMARY).read()
     except OSError:
@@ -295,6 +295,8 @@ def profiled_traffic():
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
     if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    if workload and vals.get("workload_eyes") != workload:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -317,7 +319,7 @@ def aggregate_throughput(units_per_rank: float, t_rank: float, dist=None, device
     return ws * units_per_rank / t, t
 
 
-def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk):
+def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk, workload=""):
     """Roofline of the traversal kernel, which is bound by instruction issue: the node
     records (64 B per visit) stay in L2 and DRAM traffic is essentially the output.
     achieved = algorithmic ops per launch (node visits x OPS_PER_VISIT) / kernel time;
@@ -335,7 +337,7 @@ def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk):
         "peak": peak / 1e12,
         "unit": "Tops/s",
         "frac": achieved / peak,
-        "traffic": profiled_traffic(),
+        "traffic": profiled_traffic(workload),
         "peak_kind": f"derived from {sms} SMs x 128 lanes x {mhz:.0f} MHz ({kind} sm_max_mhz)",
         "kernel": "cull_single_kernel",
         "kernel_ms": cull_ms,

@@ -10,7 +10,8 @@
 // orders the triangles by the Morton keys of their centroids and builds the same binary
 // radix tree over them; a refit then replaces the records' point boxes with triangle
 // boxes, widened so that floating-point slab tests can never reject a box that holds a
-// crossing. One thread traces one pair's shadow segment (any hit ends it).
+// crossing. Each lane of a persistent grid traces one pair's shadow segment at a time (any
+// hit ends it) and takes the next pair when it is done.
 #include <algorithm>
 #include <new>
 
@@ -168,63 +169,6 @@ __device__ __forceinline__ void load_record(const float4 *p, float4 &q0, float4 
         : "l"(p));
 }
 
-// Any triangle crossing the open segment e -> e + D?
-__device__ bool occluded(const float e[3], const float D[3], const float4 *__restrict__ nodes,
-                         const float4 *__restrict__ tris, uint32_t n, unsigned long long *flags) {
-    // a zero component is taken as 1e-30: its slab then admits exactly the boxes whose
-    // range holds e (up to 1e-30, a conservative margin), with no 0 * inf
-    float inv[3];
-    for (int c = 0; c < 3; ++c) inv[c] = __frcp_rn(D[c] == 0.0f ? 1e-30f : D[c]);
-    if (n == 1) {
-        const float4 *t = tris;
-        return segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2));
-    }
-    uint32_t stack[kStack];
-    int sp = 0;
-    uint32_t node = 0;
-    for (uint32_t guard = 0; guard < 2u * n; ++guard) {
-        float4 q0, q1, q2, q3;
-        load_record(&nodes[4 * (size_t)node], q0, q1, q2, q3);
-        const uint32_t split = __float_as_uint(q1.w), other = __float_as_uint(q3.w);
-        const uint32_t first = min(node, other), last = max(node, other);
-        if (last >= n || split < first || split >= last) {
-            atomicOr(flags, HRR_FLAG_TOPOLOGY);
-            return false;
-        }
-        const float lo0[3] = {q0.x, q0.y, q0.z}, hi0[3] = {q1.x, q1.y, q1.z};
-        const float lo1[3] = {q2.x, q2.y, q2.z}, hi1[3] = {q3.x, q3.y, q3.z};
-        const bool h0 = box_hit(e, inv, lo0, hi0), h1 = box_hit(e, inv, lo1, hi1);
-        const bool leaf0 = first == split, leaf1 = split + 1 == last;
-        if (h0 && leaf0) {
-            const float4 *t = tris + 3 * (size_t)split;
-            if (segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2))) return true;
-        }
-        if (h1 && leaf1) {
-            const float4 *t = tris + 3 * (size_t)(split + 1);
-            if (segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2))) return true;
-        }
-        const bool go0 = h0 && !leaf0, go1 = h1 && !leaf1;
-        if (go0 && go1) {
-            if (sp >= kStack) {
-                atomicOr(flags, HRR_FLAG_STACK);
-                return false;
-            }
-            stack[sp++] = split + 1;
-            node = split;
-        } else if (go0) {
-            node = split;
-        } else if (go1) {
-            node = split + 1;
-        } else if (sp > 0) {
-            node = stack[--sp];
-        } else {
-            return false;
-        }
-    }
-    atomicOr(flags, HRR_FLAG_TOPOLOGY);  // more visits than nodes: corrupt records
-    return false;
-}
-
 struct ConnectArgs {
     hrr_eyes eyes;
     uint32_t n_eyes;
@@ -240,9 +184,24 @@ struct ConnectArgs {
     uint8_t *visible;     // per pair, or NULL
     float *eye_sum;       // per eye
     unsigned long long *flags;
+    unsigned long long *cursor;  // next pair to trace (starts at 0)
 };
 
-__global__ void __launch_bounds__(kThreads) connect_kernel(const ConnectArgs A) {
+#ifndef HRR_CONNECT_REFILL_BELOW
+#define HRR_CONNECT_REFILL_BELOW 24
+#endif
+constexpr uint32_t kRefillBelow = HRR_CONNECT_REFILL_BELOW;  // refill idle lanes once fewer are busy
+
+// The outputs of pair k (eye j): weight times visibility, the visibility bit, the eye's sum.
+__device__ __forceinline__ void finish(const ConnectArgs &A, unsigned long long k, uint32_t j, float w, bool vis) {
+    const float out = vis ? w : 0.0f;
+    if (A.weight) A.weight[k] = out;
+    if (A.visible) A.visible[k] = vis ? 1 : 0;
+    if (out != 0.0f) atomicAdd(&A.eye_sum[j], out);
+}
+
+// Without a scene every connection is visible: one thread per pair, grid-stride.
+__global__ void __launch_bounds__(kThreads) weights_kernel(const ConnectArgs A) {
     const unsigned long long stride = (unsigned long long)gridDim.x * kThreads;
     for (unsigned long long k = (unsigned long long)blockIdx.x * kThreads + threadIdx.x; k < A.n_pairs; k += stride) {
         const uint2 pr = A.pairs[k];
@@ -250,22 +209,120 @@ __global__ void __launch_bounds__(kThreads) connect_kernel(const ConnectArgs A) 
             atomicOr(A.flags, HRR_FLAG_RANGE);
             continue;
         }
-        const float e[3] = {A.eyes.x[pr.x], A.eyes.y[pr.x], A.eyes.z[pr.x]};
-        const float l[3] = {A.lights.x[pr.y], A.lights.y[pr.y], A.lights.z[pr.y]};
+        const float dx = __fsub_rn(A.lights.x[pr.y], A.eyes.x[pr.x]);
+        const float dy = __fsub_rn(A.lights.y[pr.y], A.eyes.y[pr.x]);
+        const float dz = __fsub_rn(A.lights.z[pr.y], A.eyes.z[pr.x]);
         const float inten = A.lights.intensity[pr.y];
-        const float D[3] = {__fsub_rn(l[0], e[0]), __fsub_rn(l[1], e[1]), __fsub_rn(l[2], e[2])};
-        // the weight: the acceptance rule's d^2 and p, then (I / den) / p
-        float d2 = __fmul_rn(D[0], D[0]);
-        d2 = __fadd_rn(d2, __fmul_rn(D[1], D[1]));
-        d2 = __fadd_rn(d2, __fmul_rn(D[2], D[2]));
+        float d2 = __fmul_rn(dx, dx);
+        d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
+        d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
         const float den = fmaxf(d2, 1e-4f);
         const float p = fminf(1.0f, __fdiv_rn(__fmul_rn(A.tau, inten), den));
-        const float w = __fdiv_rn(__fdiv_rn(inten, den), p);
-        const bool vis = A.nodes == nullptr || !occluded(e, D, A.nodes, A.tris, A.n_tris, A.flags);
-        const float out = vis ? w : 0.0f;
-        if (A.weight) A.weight[k] = out;
-        if (A.visible) A.visible[k] = vis ? 1 : 0;
-        if (out != 0.0f) atomicAdd(&A.eye_sum[pr.x], out);
+        finish(A, k, pr.x, __fdiv_rn(__fdiv_rn(inten, den), p), true);
+    }
+}
+
+// Persistent segments: each lane traces one pair's segment, one hierarchy node per step,
+// and a warp refills its idle lanes from the global pair cursor (one atomic per refill), so
+// lanes do not idle behind the warp's longest segment. A segment ends at its first
+// crossing (occluded) or when its stack runs dry (visible).
+__global__ void __launch_bounds__(kThreads) connect_kernel(const ConnectArgs A) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    bool alive = false, more = true;
+    unsigned long long k = 0;
+    uint32_t j = 0, node = 0, steps = 0;
+    int sp = 0;
+    float w = 0.0f;
+    float e[3] = {0.f, 0.f, 0.f}, D[3] = {0.f, 0.f, 0.f}, inv[3] = {0.f, 0.f, 0.f};
+    uint32_t stack[kStack];
+    for (;;) {
+        unsigned alive_mask = __ballot_sync(0xFFFFFFFFu, alive);
+        if (more && (uint32_t)__popc(alive_mask) < kRefillBelow) {
+            const unsigned idle = ~alive_mask;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(A.cursor, (unsigned long long)__popc(idle));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (base + __popc(idle) >= A.n_pairs) more = false;
+            if (!alive) {
+                k = base + __popc(idle & lt);
+                if (k < A.n_pairs) {
+                    const uint2 pr = A.pairs[k];
+                    if (pr.x >= A.n_eyes || pr.y >= A.n_lights) {
+                        atomicOr(A.flags, HRR_FLAG_RANGE);
+                    } else {
+                        j = pr.x;
+                        e[0] = A.eyes.x[j]; e[1] = A.eyes.y[j]; e[2] = A.eyes.z[j];
+                        const float l0 = A.lights.x[pr.y], l1 = A.lights.y[pr.y], l2 = A.lights.z[pr.y];
+                        const float inten = A.lights.intensity[pr.y];
+                        D[0] = __fsub_rn(l0, e[0]); D[1] = __fsub_rn(l1, e[1]); D[2] = __fsub_rn(l2, e[2]);
+                        // the weight: the acceptance rule's d^2 and p, then (I / den) / p
+                        float d2 = __fmul_rn(D[0], D[0]);
+                        d2 = __fadd_rn(d2, __fmul_rn(D[1], D[1]));
+                        d2 = __fadd_rn(d2, __fmul_rn(D[2], D[2]));
+                        const float den = fmaxf(d2, 1e-4f);
+                        const float p = fminf(1.0f, __fdiv_rn(__fmul_rn(A.tau, inten), den));
+                        w = __fdiv_rn(__fdiv_rn(inten, den), p);
+                        if (A.n_tris == 1) {
+                            const float4 *t = A.tris;
+                            finish(A, k, j, w, !segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2)));
+                        } else {
+                            // a zero component is taken as 1e-30: its slab then admits exactly
+                            // the boxes whose range holds e (up to 1e-30, a conservative margin)
+                            for (int c = 0; c < 3; ++c) inv[c] = __frcp_rn(D[c] == 0.0f ? 1e-30f : D[c]);
+                            node = 0;
+                            sp = 0;
+                            steps = 0;
+                            alive = true;
+                        }
+                    }
+                }
+            }
+            alive_mask = __ballot_sync(0xFFFFFFFFu, alive);
+        }
+        if (alive_mask == 0u && !more) break;
+        if (!alive) continue;
+        float4 q0, q1, q2, q3;
+        load_record(&A.nodes[4 * (size_t)node], q0, q1, q2, q3);
+        const uint32_t split = __float_as_uint(q1.w), other = __float_as_uint(q3.w);
+        const uint32_t first = min(node, other), last = max(node, other);
+        if (last >= A.n_tris || split < first || split >= last || sp >= kStack || ++steps >= A.n_tris) {
+            // corrupt records: out-of-range links, an impossible depth, or more steps than
+            // the hierarchy has internal nodes
+            atomicOr(A.flags, HRR_FLAG_TOPOLOGY);
+            alive = false;
+            continue;
+        }
+        const float lo0[3] = {q0.x, q0.y, q0.z}, hi0[3] = {q1.x, q1.y, q1.z};
+        const float lo1[3] = {q2.x, q2.y, q2.z}, hi1[3] = {q3.x, q3.y, q3.z};
+        const bool h0 = box_hit(e, inv, lo0, hi0), h1 = box_hit(e, inv, lo1, hi1);
+        const bool leaf0 = first == split, leaf1 = split + 1 == last;
+        bool hit = false;
+        if (h0 && leaf0) {
+            const float4 *t = A.tris + 3 * (size_t)split;
+            hit = segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2));
+        }
+        if (!hit && h1 && leaf1) {
+            const float4 *t = A.tris + 3 * (size_t)(split + 1);
+            hit = segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2));
+        }
+        const bool go0 = h0 && !leaf0, go1 = h1 && !leaf1;
+        if (hit) {
+            finish(A, k, j, w, false);
+            alive = false;
+        } else if (go0 && go1) {
+            stack[sp++] = split + 1;
+            node = split;
+        } else if (go0) {
+            node = split;
+        } else if (go1) {
+            node = split + 1;
+        } else if (sp > 0) {
+            node = stack[--sp];
+        } else {
+            finish(A, k, j, w, true);
+            alive = false;
+        }
     }
 }
 
@@ -360,7 +417,7 @@ int hrr_connect(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, hrr_lights lights,
     DeviceGuard g(ctx->device);
     cudaStream_t st = ctx->stream;
     unsigned long long *flags = ctx->counters + 2;
-    HRR_CUDA(ctx, cudaMemsetAsync(flags, 0, sizeof(unsigned long long), st));
+    HRR_CUDA(ctx, cudaMemsetAsync(flags, 0, 2 * sizeof(unsigned long long), st));  // flags, pair cursor
     if (n_eyes) HRR_CUDA(ctx, cudaMemsetAsync(dev_eye_sum, 0, sizeof(float) * (size_t)n_eyes, st));
     if (n_pairs) {
         ConnectArgs A{};
@@ -378,13 +435,16 @@ int hrr_connect(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, hrr_lights lights,
         A.visible = dev_visible;
         A.eye_sum = dev_eye_sum;
         A.flags = flags;
+        A.cursor = ctx->counters + 3;
+        const void *fn = scene ? reinterpret_cast<const void *>(connect_kernel) : reinterpret_cast<const void *>(weights_kernel);
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, connect_kernel, kThreads, 0) != cudaSuccess || per_sm < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;
         const unsigned long long want = (n_pairs + kThreads - 1) / kThreads;
         const unsigned grid = (unsigned)std::min<unsigned long long>(want, (unsigned long long)per_sm * ctx->sm_count);
         hrr_timing_begin(ctx);
-        connect_kernel<<<grid, kThreads, 0, st>>>(A);
+        if (scene) connect_kernel<<<grid, kThreads, 0, st>>>(A);
+        else weights_kernel<<<grid, kThreads, 0, st>>>(A);
         hrr_timing_end(ctx);
         ++ctx->launches;
         HRR_CUDA(ctx, cudaGetLastError());
