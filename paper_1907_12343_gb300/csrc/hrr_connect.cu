@@ -21,13 +21,14 @@ struct hrr_scene {
     int device = 0;
     uint32_t n = 0;
     hrr_tree *tree = nullptr;  // records: child boxes of the triangles; perm: sorted -> original
-    float4 *tris = nullptr;    // sorted triangles, 3 float4 each (v0, v1, v2; w unused)
+    float *tris = nullptr;     // sorted triangles, 16 floats each: v0, e1 = v1 - v0, e2 = v2 - v0, pad
 };
 
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kStack = 128;  // >= height of the radix tree (at most 96) + 2
+constexpr int kTriFloats = 16;  // a sorted triangle's stride (64 bytes: aligned 256-bit loads)
 
 __global__ void __launch_bounds__(kThreads) centroid_kernel(const float *__restrict__ tri, uint32_t n,
                                                              float *cx, float *cy, float *cz, float *zero,
@@ -69,16 +70,20 @@ __device__ __forceinline__ void store_box(hrr_node *node, uint32_t slot, const f
 // Sorted triangles, and the bottom-up refit of the records with triangle boxes (the same
 // arrival scheme as the light refit: the second child to arrive finishes its parent).
 __global__ void __launch_bounds__(kThreads) tri_refit_kernel(const float *__restrict__ tri, const uint32_t *perm,
-                                                             uint32_t n, hrr_node *nodes, float4 *sorted,
+                                                             uint32_t n, hrr_node *nodes, float *sorted,
                                                              const uint32_t *__restrict__ leaf_parent,
                                                              const uint32_t *__restrict__ int_parent,
                                                              uint32_t *arrivals, unsigned long long *flags) {
     const uint32_t leaf = blockIdx.x * kThreads + threadIdx.x;
     if (leaf >= n) return;
     const float *t = tri + 9 * (size_t)perm[leaf];
-    sorted[3 * (size_t)leaf + 0] = make_float4(t[0], t[1], t[2], 0.0f);
-    sorted[3 * (size_t)leaf + 1] = make_float4(t[3], t[4], t[5], 0.0f);
-    sorted[3 * (size_t)leaf + 2] = make_float4(t[6], t[7], t[8], 0.0f);
+    // v0 and the edges e1, e2 (the segment test's first six roundings, done once here), so
+    // that one 256-bit load and one 32-bit load fetch a triangle
+    float *o = sorted + kTriFloats * (size_t)leaf;
+    o[0] = t[0]; o[1] = t[1]; o[2] = t[2];
+    o[3] = __fsub_rn(t[3], t[0]); o[4] = __fsub_rn(t[4], t[1]); o[5] = __fsub_rn(t[5], t[2]);
+    o[6] = __fsub_rn(t[6], t[0]); o[7] = __fsub_rn(t[7], t[1]); o[8] = __fsub_rn(t[8], t[2]);
+    for (int c = 9; c < kTriFloats; ++c) o[c] = 0.0f;
     float lo[3], hi[3];
     tri_box(t, lo, hi);
     if (n == 1) {
@@ -124,20 +129,23 @@ __global__ void __launch_bounds__(kThreads) scene_links_kernel(const hrr_node *_
     if (last == s + 1) leaf_parent[s + 1] = code | 1u; else int_parent[s + 1] = code | 1u;
 }
 
-// Open segment e -> e + D, t in (1e-4, 1 - 1e-4), against the closed triangle (v0, v1, v2):
-// Moller-Trumbore with every product and sum rounded separately (no fused operations), dot
-// products summed x + y then + z, one correctly rounded reciprocal of det.
-__device__ __forceinline__ bool segment_hits(const float e[3], const float D[3], const float4 v0, const float4 v1,
-                                             const float4 v2) {
-    const float e1x = __fsub_rn(v1.x, v0.x), e1y = __fsub_rn(v1.y, v0.y), e1z = __fsub_rn(v1.z, v0.z);
-    const float e2x = __fsub_rn(v2.x, v0.x), e2y = __fsub_rn(v2.y, v0.y), e2z = __fsub_rn(v2.z, v0.z);
+// Open segment e -> e + D, t in (1e-4, 1 - 1e-4), against the closed triangle (v0, v1, v2),
+// stored as v0, e1 = v1 - v0, e2 = v2 - v0: Moller-Trumbore with every product and sum
+// rounded separately (no fused operations), dot products summed x + y then + z, one
+// correctly rounded reciprocal of det.
+__device__ __forceinline__ bool segment_hits(const float e[3], const float D[3], const float *__restrict__ tri) {
+    float v0x, v0y, v0z, e1x, e1y, e1z, e2x, e2y;
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v0x), "=f"(v0y), "=f"(v0z), "=f"(e1x), "=f"(e1y), "=f"(e1z), "=f"(e2x), "=f"(e2y)
+        : "l"(tri));
+    const float e2z = __ldg(tri + 8);
     const float Px = __fsub_rn(__fmul_rn(D[1], e2z), __fmul_rn(D[2], e2y));
     const float Py = __fsub_rn(__fmul_rn(D[2], e2x), __fmul_rn(D[0], e2z));
     const float Pz = __fsub_rn(__fmul_rn(D[0], e2y), __fmul_rn(D[1], e2x));
     const float det = __fadd_rn(__fadd_rn(__fmul_rn(e1x, Px), __fmul_rn(e1y, Py)), __fmul_rn(e1z, Pz));
     if (det == 0.0f) return false;
     const float inv = __frcp_rn(det);
-    const float Tx = __fsub_rn(e[0], v0.x), Ty = __fsub_rn(e[1], v0.y), Tz = __fsub_rn(e[2], v0.z);
+    const float Tx = __fsub_rn(e[0], v0x), Ty = __fsub_rn(e[1], v0y), Tz = __fsub_rn(e[2], v0z);
     const float u = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(Tx, Px), __fmul_rn(Ty, Py)), __fmul_rn(Tz, Pz)), inv);
     if (!(u >= 0.0f && u <= 1.0f)) return false;
     const float Qx = __fsub_rn(__fmul_rn(Ty, e1z), __fmul_rn(Tz, e1y));
@@ -178,7 +186,7 @@ struct ConnectArgs {
     const uint2 *pairs;
     unsigned long long n_pairs;
     const float4 *nodes;  // scene, or NULL
-    const float4 *tris;
+    const float *tris;    // sorted triangles, kTriFloats each
     uint32_t n_tris;
     float *weight;        // per pair, or NULL
     uint8_t *visible;     // per pair, or NULL
@@ -264,8 +272,7 @@ __global__ void __launch_bounds__(kThreads) connect_kernel(const ConnectArgs A) 
                         const float p = fminf(1.0f, __fdiv_rn(__fmul_rn(A.tau, inten), den));
                         w = __fdiv_rn(__fdiv_rn(inten, den), p);
                         if (A.n_tris == 1) {
-                            const float4 *t = A.tris;
-                            finish(A, k, j, w, !segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2)));
+                            finish(A, k, j, w, !segment_hits(e, D, A.tris));
                         } else {
                             // a zero component is taken as 1e-30: its slab then admits exactly
                             // the boxes whose range holds e (up to 1e-30, a conservative margin)
@@ -299,12 +306,10 @@ __global__ void __launch_bounds__(kThreads) connect_kernel(const ConnectArgs A) 
         const bool leaf0 = first == split, leaf1 = split + 1 == last;
         bool hit = false;
         if (h0 && leaf0) {
-            const float4 *t = A.tris + 3 * (size_t)split;
-            hit = segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2));
+            hit = segment_hits(e, D, A.tris + kTriFloats * (size_t)split);
         }
         if (!hit && h1 && leaf1) {
-            const float4 *t = A.tris + 3 * (size_t)(split + 1);
-            hit = segment_hits(e, D, __ldg(t), __ldg(t + 1), __ldg(t + 2));
+            hit = segment_hits(e, D, A.tris + kTriFloats * (size_t)(split + 1));
         }
         const bool go0 = h0 && !leaf0, go1 = h1 && !leaf1;
         if (hit) {
@@ -366,7 +371,7 @@ int hrr_build_scene(hrr_ctx *ctx, const float *dev_tris, uint32_t n_tris, hrr_sc
     sc->n = n_tris;
     sc->tree = tree;
     uint32_t *links = nullptr;
-    cudaError_t e = cudaMallocAsync(&sc->tris, sizeof(float4) * 3 * n, st);
+    cudaError_t e = cudaMallocAsync(&sc->tris, sizeof(float) * kTriFloats * n, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&links, sizeof(uint32_t) * 3 * n, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(links, 0xFF, sizeof(uint32_t) * 2 * n, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(links + 2 * n, 0, sizeof(uint32_t) * n, st);
