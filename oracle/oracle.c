@@ -477,7 +477,90 @@ static void boxes_from_leaves(or_tree *t)
     }
 }
 
+/* Cost-driven split of the range [f, l] (l > f) over the same leaf order: among the
+ * candidate splits k (children [f, k] and [k+1, l]), the one minimising
+ *     C(k) = m_L (A_L + 1e-4) c_L + m_R (A_R + 1e-4) c_R,
+ * with c the child's light count, m its maximum intensity clamped at 0 and A half the
+ * surface area of its box (dx dy + dy dz + dz dx), all in double, each operation rounded
+ * separately, in this order. A node is visited about in proportion to its count times its
+ * maximum intensity over its squared distance, so lowering C lowers the expected visits.
+ * Candidates: with q = ceil(m / 1024) for a range of m lights, every k with k - f + 1 a
+ * multiple of q (all k when m <= 1024). Ties go to the split nearest the middle (the least
+ * |c_L - c_R|), then to the smaller k. suf holds 7 doubles per leaf of scratch. */
+static uint32_t cost_split(const or_tree *t, uint32_t f, uint32_t l, double *suf)
+{
+    /* suffix boxes and maxima: suf[7 * (i - f)] = lo xyz, hi xyz, max intensity of [i, l] */
+    for (uint32_t i = l + 1; i-- > f;) {
+        double *o = &suf[7 * (uint64_t)(i - f)];
+        const float *p = &t->pos[3 * (uint64_t)i];
+        for (int c = 0; c < 3; ++c)
+            o[c] = o[3 + c] = p[c];
+        o[6] = t->inten[i];
+        if (i < l) {
+            const double *q = o + 7;
+            for (int c = 0; c < 3; ++c) {
+                o[c] = fmin(o[c], q[c]);
+                o[3 + c] = fmax(o[3 + c], q[3 + c]);
+            }
+            o[6] = fmax(o[6], q[6]);
+        }
+    }
+    const uint64_t m_all = (uint64_t)l - f + 1;
+    const uint64_t q = (m_all + 1023) / 1024;
+    double lo[3], hi[3], m = -INFINITY;
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = INFINITY;
+        hi[c] = -INFINITY;
+    }
+    double best = INFINITY;
+    uint32_t best_k = f;
+    int64_t best_dist = INT64_MAX;
+    for (uint32_t k = f; k < l; ++k) {
+        const float *p = &t->pos[3 * (uint64_t)k];
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fmin(lo[c], (double)p[c]);
+            hi[c] = fmax(hi[c], (double)p[c]);
+        }
+        m = fmax(m, (double)t->inten[k]);
+        if (((uint64_t)k - f + 1) % q != 0)
+            continue;
+        const double *r = &suf[7 * (uint64_t)(k + 1 - f)];
+        double dxl = hi[0] - lo[0], dyl = hi[1] - lo[1], dzl = hi[2] - lo[2];
+        double dxr = r[3] - r[0], dyr = r[4] - r[1], dzr = r[5] - r[2];
+        double al = dxl * dyl + dyl * dzl + dzl * dxl;
+        double ar = dxr * dyr + dyr * dzr + dzr * dxr;
+        double ml = fmax(m, 0.0), mr = fmax(r[6], 0.0);
+        double cl = (double)(k - f + 1), cr = (double)(l - k);
+        double cost = ml * (al + 1e-4) * cl + mr * (ar + 1e-4) * cr;
+        int64_t dist = (int64_t)(k - f + 1) - (int64_t)(l - k);
+        if (dist < 0)
+            dist = -dist;
+        if (cost < best || (cost == best && dist < best_dist)) {
+            best = cost;
+            best_k = k;
+            best_dist = dist;
+        }
+    }
+    return best_k;
+}
+
+/* Depth (root = 1) up to which the cost rule splits; deeper nodes take the radix split, which
+ * bounds the height by this depth plus 96 whatever the intensities. */
+enum { kCostDepthMax = 48 };
+
+static or_tree *tree_build(const float *pos, const float *intensity, uint32_t n, int cost_rule);
+
 or_tree *or_tree_build(const float *pos, const float *intensity, uint32_t n)
+{
+    return tree_build(pos, intensity, n, 0);
+}
+
+or_tree *or_tree_build_cost(const float *pos, const float *intensity, uint32_t n)
+{
+    return tree_build(pos, intensity, n, 1);
+}
+
+static or_tree *tree_build(const float *pos, const float *intensity, uint32_t n, int cost_rule)
 {
     if (n == 0)
         return NULL;
@@ -519,16 +602,21 @@ or_tree *or_tree_build(const float *pos, const float *intensity, uint32_t n)
      * its end keys changes from 0 to 1. The root is internal node 0; the children of a
      * node split at s are numbered s and s+1. */
     typedef struct { uint32_t id, f, l, depth; } job;
-    job *stack = (job *)malloc(sizeof(job) * 256);
+    job *stack = (job *)malloc(sizeof(job) * 512);
+    double *suf = cost_rule ? (double *)malloc(sizeof(double) * 7 * (uint64_t)n) : NULL;
     int sp = 0;
     stack[sp++] = (job){0, 0, n - 1, 1};
     while (sp > 0) {
         job j = stack[--sp];
-        int bit = highest_difference(t, j.f, j.l);
         uint32_t s = j.f;
-        for (uint32_t k = j.f; k < j.l; ++k)
-            if (digit_of(t, k, bit) == 0)
-                s = k;
+        if (cost_rule && j.depth <= kCostDepthMax) {
+            s = cost_split(t, j.f, j.l, suf);
+        } else {
+            int bit = highest_difference(t, j.f, j.l);
+            for (uint32_t k = j.f; k < j.l; ++k)
+                if (digit_of(t, k, bit) == 0)
+                    s = k;
+        }
         t->first[j.id] = j.f;
         t->last[j.id] = j.l;
         t->split[j.id] = s;
@@ -540,6 +628,7 @@ or_tree *or_tree_build(const float *pos, const float *intensity, uint32_t n)
             stack[sp++] = (job){s + 1, s + 1, j.l, j.depth + 1};
     }
     free(stack);
+    free(suf);
 
     boxes_from_leaves(t);
     return t;
@@ -697,7 +786,7 @@ or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint1
                 list_push(&lists[j], 0);
             continue;
         }
-        uint32_t stack[128];
+        uint32_t stack[256]; /* depth-first: at most one pending node per level, height <= 144 */
         int sp = 0;
         stack[sp++] = 0;
         uint64_t v_count = 0;

@@ -1,0 +1,121 @@
+"""Cost-driven splits over the Morton leaf order (the hierarchy the benchmark builds): the
+oracle's rule against closed forms, a float64 restatement of the rule, tree validity, the
+height bound, and hierarchical culling equal to flat culling (the leaf order, and so the
+accepted set, are the radix tree's)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _check_tree(t):
+    n = t.n
+    if n == 1:
+        return
+    seen = np.zeros(n, int)
+    stack = [0]
+    while stack:
+        k = stack.pop()
+        f, l, s = int(t.first[k]), int(t.last[k]), int(t.split[k])
+        assert f <= s < l and k in (f, l)
+        for cf, cl, cid in ((f, s, s), (s + 1, l, s + 1)):
+            if cf == cl:
+                seen[cf] += 1
+            else:
+                assert t.first[cid] == cf and t.last[cid] == cl
+                stack.append(cid)
+    assert np.all(seen == 1)
+    assert t.height <= 48 + 96
+
+
+def test_dark_lights_split_in_the_middle():
+    # zero intensities: every candidate costs exactly 0, ties go to the middle, so the tree
+    # is perfectly balanced (2048 lights also exercise the candidate stride q = 2)
+    for n in (8, 16, 64, 2048):
+        rng = np.random.default_rng(n)
+        pos = rng.random((n, 3)).astype(np.float32)
+        t = oracle.Tree(pos, np.zeros(n, np.float32), topology="cost")
+        _check_tree(t)
+        assert t.height == int(np.log2(n))
+        assert t.split[0] == n // 2 - 1
+
+
+def test_two_clusters_are_separated_at_the_root():
+    rng = np.random.default_rng(1)
+    a = (0.1 + 0.01 * rng.random((300, 3))).astype(np.float32)
+    b = (0.8 + 0.01 * rng.random((200, 3))).astype(np.float32)
+    t = oracle.Tree(np.concatenate([a, b]), np.ones(500, np.float32), topology="cost")
+    _check_tree(t)
+    left = set(t.perm[: int(t.split[0]) + 1].tolist())
+    assert left == set(range(300))
+
+
+def _rule(pos, inten, f, l):
+    """The split rule restated in float64 numpy: candidates every q-th split, cost, ties."""
+    m = l - f + 1
+    q = -(-m // 1024)
+    P = pos[f:l + 1].astype(np.float64)
+    I = inten[f:l + 1].astype(np.float64)
+    best = None
+    for k in range(f, l):
+        if (k - f + 1) % q:
+            continue
+        L, R = P[: k - f + 1], P[k - f + 1:]
+        dl, dr = L.max(0) - L.min(0), R.max(0) - R.min(0)
+        al = dl[0] * dl[1] + dl[1] * dl[2] + dl[2] * dl[0]
+        ar = dr[0] * dr[1] + dr[1] * dr[2] + dr[2] * dr[0]
+        ml, mr = max(I[: k - f + 1].max(), 0.0), max(I[k - f + 1:].max(), 0.0)
+        cl, cr = k - f + 1, l - k
+        cost = ml * (al + 1e-4) * cl + mr * (ar + 1e-4) * cr
+        key = (cost, abs(cl - cr), k)
+        best = key if best is None or key < best else best
+    return best[2]
+
+
+@pytest.mark.parametrize("n,seed", [(2, 1), (3, 2), (40, 3), (1000, 4), (5000, 5)])
+def test_splits_follow_the_rule(n, seed):
+    s = synth.scene_frame(width=8, height=8, n_lights=n, seed=seed)
+    t = oracle.Tree(s.light_pos, s.intensity, topology="cost")
+    _check_tree(t)
+    ks = [0] + [k for k in range(1, n - 1) if t.first[k] != t.last[k]][:6]
+    for k in ks:
+        f, l = int(t.first[k]), int(t.last[k])
+        if l - f + 1 > 1 and (k == 0 or l - f < 3000):
+            assert t.split[k] == _rule(t.pos, t.inten, f, l)
+
+
+@pytest.mark.parametrize("case", ["uniform", "mixture", "duplicates", "zero", "tiny", "chain"])
+def test_hierarchical_culling_equals_flat(case):
+    if case == "uniform":
+        s = dict(synth.scene_uniform(n_lights=3000, seed=91))
+    else:
+        s = dict(synth.scene_frame(width=24, height=16, n_lights=4001, tile_w=16, tile_h=16, target=24.0, seed=92))
+    if case == "duplicates":
+        s["light_pos"] = np.repeat(s["light_pos"][:500], 8, axis=0)[:4001]
+    if case == "zero":
+        s["intensity"] = np.where(np.arange(4001) % 3 == 0, 0.0, s["intensity"]).astype(np.float32)
+    if case == "tiny":
+        s["light_pos"], s["intensity"] = s["light_pos"][:17], s["intensity"][:17] * 50
+    if case == "chain":  # intensities that grow along the Morton order push the cost rule to chains
+        t0 = oracle.Tree(s["light_pos"], s["intensity"])
+        inten = np.empty(len(s["intensity"]), np.float32)
+        inten[t0.perm] = np.exp(np.linspace(-20, 20, len(inten))).astype(np.float32)
+        s["intensity"] = inten
+    t = oracle.Tree(s["light_pos"], s["intensity"], topology="cost")
+    _check_tree(t)
+    flat = oracle.cull_flat(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"])
+    hier = oracle.cull_hier(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"])
+    key = lambda p: np.sort(p.astype(np.uint64)[:, 0] << np.uint64(32) | p.astype(np.uint64)[:, 1])
+    assert np.array_equal(key(flat["pairs"]), key(hier["pairs"]))
+    radix = oracle.Tree(s["light_pos"], s["intensity"])
+    assert np.array_equal(radix.perm, t.perm)
+
+
+def test_fewer_visits_than_the_radix_tree_on_the_frame_workload():
+    s = synth.scene_frame(width=48, height=27, n_lights=1 << 15, tile_w=16, tile_h=16, target=48.0, seed=93)
+    v = {}
+    for topo in ("radix", "cost"):
+        t = oracle.Tree(s.light_pos, s.intensity, topology=topo)
+        v[topo] = oracle.cull_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)["total_visits"]
+    assert v["cost"] < 0.92 * v["radix"]
