@@ -152,7 +152,7 @@ def run_ours(args):
     tau = float(s.tau)
 
     def step():
-        tree = ctx.build_light_tree(*L)
+        tree = ctx.build_light_tree(*L, topology=TOPOLOGY)
         st, cnt = ctx.cull(*E, px, py, tree, tau, pairs)
         tree.free()
         if st != hrr.HRR_OK:
@@ -162,7 +162,7 @@ def run_ours(args):
     # warm-up
     for _ in range(args.warmup):
         cnt, _ = step()
-    tree = ctx.build_light_tree(*L)
+    tree = ctx.build_light_tree(*L, topology=TOPOLOGY)
     height = tree.height
     tree.free()
 
@@ -240,7 +240,7 @@ def run_ours(args):
             "config": {"workload": f"frame {args.eyes} eyes x {n_l} Gaussian-mixture lights, "
                                    "64x64 blue-noise tile, ~64 accepted/eye",
                        "n_eyes": n_e, "n_lights": n_l, "tau": tau, "tree_height": height,
-                       "step": "build light tree + cull all eyes",
+                       "step": "build light tree + cull all eyes", "topology": TOPOLOGY,
                        "l2": "flushed between steps (512 MiB write outside the step events)",
                        "parallelism": f"replicas x{ws}"},
             "accepted_pairs": int(cnt), "accepted_per_eye": cnt / n_e, "node_visits": int(V),
@@ -269,6 +269,7 @@ def run_ours(args):
 # 51 integer ops + 0.774 inherited minima x 2 + 0.037 leaf tests x 17.
 OPS_PER_VISIT = 1.963 * 27 + 0.977 * 51 + 0.774 * 2 + 0.037 * 17
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_1920x1080.md")
+TOPOLOGY = "cost"  # hierarchy shape of the benchmarked builds (set from --topology)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
                   for f in ("hrr_cull.cu", "hrr_math.cuh")]
 
@@ -282,9 +283,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload=""):
+def profiled_traffic(workload="", topology=None):
     """DRAM bytes per cull launch from the committed ncu summary, if it was taken on the
-    current kernel source and on this workload (null otherwise)."""
+    current kernel source, on this workload and on this hierarchy shape (null otherwise)."""
     try:
         text = open(PROFILE_SUMMARY).read()
     except OSError:
@@ -297,6 +298,8 @@ def profiled_traffic(workload=""):
     if vals.get("kernel_source_sha256") != kernel_source_hash():
         return None
     if workload and vals.get("workload_eyes") != workload:
+        return None
+    if vals.get("topology") != (topology or TOPOLOGY):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -372,7 +375,7 @@ def run_e2e(ctx, s, dev, stream, args, cap):
             t0 = time.perf_counter()
             for h, d in zip(host_l + host_e, dev_l + dev_e):
                 d.copy_(h, non_blocking=True)
-            tree = ctx.build_light_tree(*dev_l)
+            tree = ctx.build_light_tree(*dev_l, topology=TOPOLOGY)
             st, cnt = ctx.cull(*dev_e[:3], dev_e[3], dev_e[4], tree, float(s.tau), pairs)
             tree.free()
             if st != hrr.HRR_OK:
@@ -402,7 +405,7 @@ def upload_frames(ctx, frames_np, dev):
         lp = torch.from_numpy(s.light_pos).to(dev)
         ep = torch.from_numpy(s.eye_pos).to(dev)
         L = [lp[:, k].contiguous() for k in range(3)] + [torch.from_numpy(s.intensity).to(dev)]
-        tree = ctx.build_light_tree(*L)
+        tree = ctx.build_light_tree(*L, topology=TOPOLOGY)
         out.append({"lights": L, "x": ep[:, 0].contiguous(), "y": ep[:, 1].contiguous(), "z": ep[:, 2].contiguous(),
                     "px": torch.from_numpy(s.px.view(np.int16)).to(dev),
                     "py": torch.from_numpy(s.py.view(np.int16)).to(dev),
@@ -540,7 +543,7 @@ def run_refit(ctx, L, dev, stream, reps=5):
     gen.manual_seed(17)
     moved = [torch.clamp(c + (torch.rand(c.shape, generator=gen, device=dev) - 0.5) * 0.04, 0.0, 1.0).contiguous()
              for c in L[:3]] + [L[3]]
-    tree = ctx.build_light_tree(*L)
+    tree = ctx.build_light_tree(*L, topology=TOPOLOGY)
     t_refit, t_build = [], []
     with torch.cuda.stream(stream):
         for k in range(reps + 1):
@@ -554,7 +557,7 @@ def run_refit(ctx, L, dev, stream, reps=5):
         for k in range(reps + 1):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            t2 = ctx.build_light_tree(*L)
+            t2 = ctx.build_light_tree(*L, topology=TOPOLOGY)
             b.record(stream)
             b.synchronize()
             t2.free()
@@ -671,7 +674,7 @@ def cpu_baseline(s, target_seconds=15.0):
     import oracle
     n_e, n_l = len(s.eye_pos), len(s.light_pos)
     t0 = time.perf_counter()
-    tree = oracle.Tree(s.light_pos, s.intensity)
+    tree = oracle.Tree(s.light_pos, s.intensity, topology=TOPOLOGY)
     t_build = time.perf_counter() - t0
     n = 512
     while True:
@@ -697,7 +700,7 @@ def run_reference(args):
     s = workload(args)
     n_e, n_l = len(s.eye_pos), len(s.light_pos)
     t0 = time.perf_counter()
-    tree = oracle.Tree(s.light_pos, s.intensity)
+    tree = oracle.Tree(s.light_pos, s.intensity, topology=TOPOLOGY)
     t_build = time.perf_counter() - t0
     n = args.ref_eyes
     ids = _oracle_sample(s, n)
@@ -736,11 +739,15 @@ def main(argv=None):
     ap.add_argument("--ref-eyes", type=int, default=2048)
     ap.add_argument("--eyes", default="1920x1080", help="frame size WxH (one eye per pixel)")
     ap.add_argument("--lights", type=int, default=1 << 20)
+    ap.add_argument("--topology", choices=["cost", "radix"], default="cost",
+                    help="hierarchy shape over the Morton order (the same accepted set)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-frames", type=int, default=64, help="0 skips the batched/served forms")
     ap.add_argument("--served-jobs", type=int, default=256, help="0 skips the served form")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    global TOPOLOGY
+    TOPOLOGY = args.topology
     if args.impl == "reference":
         run_reference(args)
     else:

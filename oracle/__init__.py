@@ -99,9 +99,10 @@ def lib():
             L.or_node_culls.argtypes = [f32, P, P, f32, P, u32]
             L.or_morton.restype = u64
             L.or_morton.argtypes = [f32, f32, f32]
-            for nm in ("or_tree_build", "or_tree_build_cost"):
-                getattr(L, nm).restype = C.POINTER(_Tree)
-                getattr(L, nm).argtypes = [P, P, u32]
+            L.or_tree_build.restype = C.POINTER(_Tree)
+            L.or_tree_build.argtypes = [P, P, u32]
+            L.or_tree_build_cost.restype = C.POINTER(_Tree)
+            L.or_tree_build_cost.argtypes = [P, P, u32, u32]
             L.or_tree_free.restype = None
             L.or_tree_free.argtypes = [C.POINTER(_Tree)]
             L.or_tree_refit.restype = None
@@ -216,12 +217,16 @@ def morton(x, y, z) -> int:
 class Tree:
     """Oracle light hierarchy: Morton-sorted leaves and a top-down binary radix tree."""
 
-    def __init__(self, light_pos: np.ndarray, intensity: np.ndarray, topology: str = "radix"):
+    def __init__(self, light_pos: np.ndarray, intensity: np.ndarray, topology: str = "radix", cost_depth: int = 0):
         self._pos = np.ascontiguousarray(light_pos, dtype=np.float32).reshape(-1, 3)
         self._inten = np.ascontiguousarray(intensity, dtype=np.float32)
         self.n = len(self._inten)
-        build = {"radix": lib().or_tree_build, "cost": lib().or_tree_build_cost}[topology]
-        self._t = build(_ptr(self._pos), _ptr(self._inten), self.n)
+        if topology == "radix":
+            self._t = lib().or_tree_build(_ptr(self._pos), _ptr(self._inten), self.n)
+        elif topology == "cost":
+            self._t = lib().or_tree_build_cost(_ptr(self._pos), _ptr(self._inten), self.n, cost_depth)
+        else:
+            raise ValueError(f"unknown topology {topology!r}")
         if not self._t:
             raise ValueError("empty light set")
         t = self._t.contents

@@ -481,57 +481,54 @@ static void boxes_from_leaves(or_tree *t)
  * candidate splits k (children [f, k] and [k+1, l]), the one minimising
  *     C(k) = m_L (A_L + 1e-4) c_L + m_R (A_R + 1e-4) c_R,
  * with c the child's light count, m its maximum intensity clamped at 0 and A half the
- * surface area of its box (dx dy + dy dz + dz dx), all in double, each operation rounded
- * separately, in this order. A node is visited about in proportion to its count times its
- * maximum intensity over its squared distance, so lowering C lowers the expected visits.
- * Candidates: with q = ceil(m / 1024) for a range of m lights, every k with k - f + 1 a
- * multiple of q (all k when m <= 1024). Ties go to the split nearest the middle (the least
- * |c_L - c_R|), then to the smaller k. suf holds 7 doubles per leaf of scratch. */
-static uint32_t cost_split(const or_tree *t, uint32_t f, uint32_t l, double *suf)
+ * surface area of its box (dx dy + dy dz + dz dx), all in float, each operation rounded
+ * separately, in this order (the counts converted to float with rounding to nearest). A
+ * node is visited about in proportion to its count times its maximum intensity over its
+ * squared distance, so lowering C lowers the expected visits. Every k in [f, l) is a
+ * candidate; a non-finite C never wins. Ties go to the split nearest the middle (the least
+ * |c_L - c_R|), then to the smaller k; with no finite C the split is f. suf holds 7 floats
+ * per leaf of scratch. */
+static uint32_t cost_split(const or_tree *t, uint32_t f, uint32_t l, float *suf)
 {
     /* suffix boxes and maxima: suf[7 * (i - f)] = lo xyz, hi xyz, max intensity of [i, l] */
     for (uint32_t i = l + 1; i-- > f;) {
-        double *o = &suf[7 * (uint64_t)(i - f)];
+        float *o = &suf[7 * (uint64_t)(i - f)];
         const float *p = &t->pos[3 * (uint64_t)i];
         for (int c = 0; c < 3; ++c)
             o[c] = o[3 + c] = p[c];
         o[6] = t->inten[i];
         if (i < l) {
-            const double *q = o + 7;
+            const float *q = o + 7;
             for (int c = 0; c < 3; ++c) {
-                o[c] = fmin(o[c], q[c]);
-                o[3 + c] = fmax(o[3 + c], q[3 + c]);
+                o[c] = fminf(o[c], q[c]);
+                o[3 + c] = fmaxf(o[3 + c], q[3 + c]);
             }
-            o[6] = fmax(o[6], q[6]);
+            o[6] = fmaxf(o[6], q[6]);
         }
     }
-    const uint64_t m_all = (uint64_t)l - f + 1;
-    const uint64_t q = (m_all + 1023) / 1024;
-    double lo[3], hi[3], m = -INFINITY;
+    float lo[3], hi[3], m = -INFINITY;
     for (int c = 0; c < 3; ++c) {
         lo[c] = INFINITY;
         hi[c] = -INFINITY;
     }
-    double best = INFINITY;
+    float best = INFINITY;
     uint32_t best_k = f;
     int64_t best_dist = INT64_MAX;
     for (uint32_t k = f; k < l; ++k) {
         const float *p = &t->pos[3 * (uint64_t)k];
         for (int c = 0; c < 3; ++c) {
-            lo[c] = fmin(lo[c], (double)p[c]);
-            hi[c] = fmax(hi[c], (double)p[c]);
+            lo[c] = fminf(lo[c], p[c]);
+            hi[c] = fmaxf(hi[c], p[c]);
         }
-        m = fmax(m, (double)t->inten[k]);
-        if (((uint64_t)k - f + 1) % q != 0)
-            continue;
-        const double *r = &suf[7 * (uint64_t)(k + 1 - f)];
-        double dxl = hi[0] - lo[0], dyl = hi[1] - lo[1], dzl = hi[2] - lo[2];
-        double dxr = r[3] - r[0], dyr = r[4] - r[1], dzr = r[5] - r[2];
-        double al = dxl * dyl + dyl * dzl + dzl * dxl;
-        double ar = dxr * dyr + dyr * dzr + dzr * dxr;
-        double ml = fmax(m, 0.0), mr = fmax(r[6], 0.0);
-        double cl = (double)(k - f + 1), cr = (double)(l - k);
-        double cost = ml * (al + 1e-4) * cl + mr * (ar + 1e-4) * cr;
+        m = fmaxf(m, t->inten[k]);
+        const float *r = &suf[7 * (uint64_t)(k + 1 - f)];
+        float dxl = hi[0] - lo[0], dyl = hi[1] - lo[1], dzl = hi[2] - lo[2];
+        float dxr = r[3] - r[0], dyr = r[4] - r[1], dzr = r[5] - r[2];
+        float al = dxl * dyl + dyl * dzl + dzl * dxl;
+        float ar = dxr * dyr + dyr * dzr + dzr * dxr;
+        float ml = fmaxf(m, 0.0f), mr = fmaxf(r[6], 0.0f);
+        float cl = (float)(k - f + 1), cr = (float)(l - k);
+        float cost = ml * (al + 1e-4f) * cl + mr * (ar + 1e-4f) * cr;
         int64_t dist = (int64_t)(k - f + 1) - (int64_t)(l - k);
         if (dist < 0)
             dist = -dist;
@@ -544,23 +541,22 @@ static uint32_t cost_split(const or_tree *t, uint32_t f, uint32_t l, double *suf
     return best_k;
 }
 
-/* Depth (root = 1) up to which the cost rule splits; deeper nodes take the radix split, which
- * bounds the height by this depth plus 96 whatever the intensities. */
-enum { kCostDepthMax = 48 };
-
-static or_tree *tree_build(const float *pos, const float *intensity, uint32_t n, int cost_rule);
+static or_tree *tree_build(const float *pos, const float *intensity, uint32_t n, uint32_t cost_depth);
 
 or_tree *or_tree_build(const float *pos, const float *intensity, uint32_t n)
 {
     return tree_build(pos, intensity, n, 0);
 }
 
-or_tree *or_tree_build_cost(const float *pos, const float *intensity, uint32_t n)
+/* Cost splits for the nodes of depth (root = 1) up to cost_depth (0 means 48); deeper
+ * nodes take the radix split, which bounds the height by cost_depth + 96 whatever the
+ * intensities. */
+or_tree *or_tree_build_cost(const float *pos, const float *intensity, uint32_t n, uint32_t cost_depth)
 {
-    return tree_build(pos, intensity, n, 1);
+    return tree_build(pos, intensity, n, cost_depth ? cost_depth : 48);
 }
 
-static or_tree *tree_build(const float *pos, const float *intensity, uint32_t n, int cost_rule)
+static or_tree *tree_build(const float *pos, const float *intensity, uint32_t n, uint32_t cost_depth)
 {
     if (n == 0)
         return NULL;
@@ -603,13 +599,13 @@ static or_tree *tree_build(const float *pos, const float *intensity, uint32_t n,
      * node split at s are numbered s and s+1. */
     typedef struct { uint32_t id, f, l, depth; } job;
     job *stack = (job *)malloc(sizeof(job) * 512);
-    double *suf = cost_rule ? (double *)malloc(sizeof(double) * 7 * (uint64_t)n) : NULL;
+    float *suf = cost_depth ? (float *)malloc(sizeof(float) * 7 * (uint64_t)n) : NULL;
     int sp = 0;
     stack[sp++] = (job){0, 0, n - 1, 1};
     while (sp > 0) {
         job j = stack[--sp];
         uint32_t s = j.f;
-        if (cost_rule && j.depth <= kCostDepthMax) {
+        if (j.depth <= cost_depth) {
             s = cost_split(t, j.f, j.l, suf);
         } else {
             int bit = highest_difference(t, j.f, j.l);

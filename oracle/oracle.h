@@ -72,8 +72,9 @@ typedef struct or_tree {
 } or_tree;
 
 or_tree *or_tree_build(const float *pos, const float *intensity, uint32_t n);
-/* The same leaf order with cost-driven splits down to depth 48 (radix splits below). */
-or_tree *or_tree_build_cost(const float *pos, const float *intensity, uint32_t n);
+/* The same leaf order with cost-driven splits down to depth cost_depth (0: 48), radix
+ * splits below. */
+or_tree *or_tree_build_cost(const float *pos, const float *intensity, uint32_t n, uint32_t cost_depth);
 void or_tree_free(or_tree *t);
 /* New positions (3 per light) and intensities for the same lights (indexed by original id):
  * the leaf order and topology stay, boxes and maximum intensities are recomputed. */

@@ -90,6 +90,14 @@ class hrr_cull_opts(C.Structure):
                 ("sample_index", C.c_uint32)]
 
 
+class hrr_build_opts(C.Structure):
+    _fields_ = [("topology", C.c_int), ("cost_depth", C.c_uint32)]
+
+
+HRR_TOPOLOGY_RADIX, HRR_TOPOLOGY_COST = 0, 1
+TOPOLOGIES = {"radix": HRR_TOPOLOGY_RADIX, "cost": HRR_TOPOLOGY_COST}
+
+
 class hrr_tuning(C.Structure):
     _fields_ = [("rangemin_variant", C.c_int), ("blocks_per_sm", C.c_uint32)]
 
@@ -121,6 +129,7 @@ _SIGS = {
     "hrr_set_shift_tile": (_i32, [_P, _P, _u32, _u32]),
     "hrr_set_shift_tile_3d": (_i32, [_P, _P, _u32, _u32, _u32]),
     "hrr_refit_light_tree": (_i32, [_P, _P, hrr_lights]),
+    "hrr_build_light_tree_ex": (_i32, [_P, hrr_lights, _u32, C.POINTER(hrr_build_opts), C.POINTER(_P)]),
     "hrr_build_scene": (_i32, [_P, _P, _u32, C.POINTER(_P)]),
     "hrr_free_scene": (_i32, [_P, _P]),
     "hrr_connect": (_i32, [_P, hrr_eyes, _u32, hrr_lights, _u32, _f32, _P, _u64, _P, _P, _P, _P]),
@@ -225,11 +234,14 @@ class Context:
             self.check(hrr_set_shift_tile(self.handle, tile.ctypes.data, w, h))
 
     # -- hierarchy -------------------------------------------------------------------------
-    def build_light_tree(self, x, y, z, intensity) -> "Tree":
+    def build_light_tree(self, x, y, z, intensity, topology: str = "radix", cost_depth: int = 0) -> "Tree":
+        """Hierarchy over the lights; topology "radix" (binary radix tree) or "cost"
+        (cost-driven splits over the same leaf order down to depth ``cost_depth``, 0 = 48)."""
         n = int(x.numel())
         L = hrr_lights(_ptr(x), _ptr(y), _ptr(z), _ptr(intensity))
         t = _P()
-        self.check(hrr_build_light_tree(self.handle, L, n, C.byref(t)))
+        opts = hrr_build_opts(TOPOLOGIES[topology], cost_depth)
+        self.check(hrr_build_light_tree_ex(self.handle, L, n, C.byref(opts), C.byref(t)))
         return Tree(self, t)
 
     def refit_light_tree(self, tree: "Tree", x, y, z, intensity):

@@ -141,7 +141,17 @@ int hrr_kernel_time(hrr_ctx *ctx, double *ms, uint64_t *launches) {
 }
 
 int hrr_build_light_tree(hrr_ctx *ctx, hrr_lights lights, uint32_t n_lights, hrr_tree **out) {
+    return hrr_build_light_tree_ex(ctx, lights, n_lights, nullptr, out);
+}
+
+int hrr_build_light_tree_ex(hrr_ctx *ctx, hrr_lights lights, uint32_t n_lights, const hrr_build_opts *opts,
+                            hrr_tree **out) {
     if (!ctx) return HRR_ERR_INVALID_ARG;
+    const int topology = opts ? opts->topology : HRR_TOPOLOGY_RADIX;
+    if (topology != HRR_TOPOLOGY_RADIX && topology != HRR_TOPOLOGY_COST)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "unknown topology");
+    const uint32_t cost_depth = opts && opts->cost_depth ? opts->cost_depth : 48u;
+    if (cost_depth > 64u) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "cost_depth must be in [0, 64]");
     if (!out) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n_lights == 0 || n_lights > 0x7FFFFFFFu)
@@ -149,7 +159,7 @@ int hrr_build_light_tree(hrr_ctx *ctx, hrr_lights lights, uint32_t n_lights, hrr
     if (!lights.x || !lights.y || !lights.z || !lights.intensity)
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "a light array is NULL");
     DeviceGuard g(ctx->device);
-    return hrr_build_impl(ctx, lights, n_lights, out);
+    return hrr_build_impl(ctx, lights, n_lights, out, topology, cost_depth);
 }
 
 int hrr_free_light_tree(hrr_ctx *ctx, hrr_tree *tree) {

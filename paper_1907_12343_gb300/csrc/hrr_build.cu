@@ -13,6 +13,8 @@
 //   5. refit_kernel      bottom-up boxes / maximum intensities with one atomic counter per
 //                        node (the second child to finish computes the parent), written
 //                        straight into the parent's 64-byte record.
+#include <algorithm>
+
 #include "hrr_internal.cuh"
 
 namespace {
@@ -73,27 +75,53 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint64_t *__
     hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive prefix sum of `total` counts in place, one block of 1024 threads.
-__global__ void __launch_bounds__(1024) exclusive_scan_kernel(uint32_t *data, uint64_t total) {
-    __shared__ uint32_t sums[1024];
-    const uint64_t per = (total + 1023) / 1024;
-    const uint64_t beg = min((uint64_t)threadIdx.x * per, total);
-    const uint64_t end = min(beg + per, total);
-    uint32_t s = 0;
-    for (uint64_t i = beg; i < end; ++i) s += data[i];
-    sums[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const uint32_t v = threadIdx.x >= (unsigned)off ? sums[threadIdx.x - off] : 0u;
-        __syncthreads();
-        sums[threadIdx.x] += v;
-        __syncthreads();
+// Exclusive prefix sum, in place, of the digit-major histogram hist[d * nblocks + b]
+// (256 digits): one block; a warp scans one digit's row at a time (coalesced, with a
+// running carry), then one warp scans the 256 digit totals and every row adds its base.
+__global__ void __launch_bounds__(1024) exclusive_scan_kernel(uint32_t *hist, uint32_t nblocks) {
+    __shared__ uint32_t base[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = warp; d < 256; d += 32) {
+        uint32_t *row = hist + (uint64_t)d * nblocks;
+        uint32_t carry = 0;
+        for (uint32_t b0 = 0; b0 < nblocks; b0 += 32) {
+            const uint32_t b = b0 + lane;
+            const uint32_t v = b < nblocks ? row[b] : 0u;
+            uint32_t x = v;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (b < nblocks) row[b] = carry + x - v;
+            carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+        }
+        if (lane == 0) base[d] = carry;
     }
-    uint32_t run = threadIdx.x ? sums[threadIdx.x - 1] : 0u;
-    for (uint64_t i = beg; i < end; ++i) {
-        const uint32_t v = data[i];
-        data[i] = run;
-        run += v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t v[8], s = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v[k] = base[lane * 8 + k];
+            s += v[k];
+        }
+        uint32_t x = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t run = x - s;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            base[lane * 8 + k] = run;
+            run += v[k];
+        }
+    }
+    __syncthreads();
+    for (int d = warp; d < 256; d += 32) {
+        uint32_t *row = hist + (uint64_t)d * nblocks;
+        const uint32_t add = base[d];
+        for (uint32_t b = lane; b < nblocks; b += 32) row[b] += add;
     }
 }
 
@@ -300,9 +328,569 @@ T *carve(char *&p, size_t count) {
     return r;
 }
 
+// ------------------------------------------------------------------------------------
+// Cost-driven topology over the Morton order
+// ------------------------------------------------------------------------------------
+//
+// A top-down build, one level per pass: every range [f, l] of the level splits at the k
+// (children [f, k], [k+1, l]) that minimises
+//     C(k) = m_L (A_L + 1e-4) c_L + m_R (A_R + 1e-4) c_R
+// (c light count, m maximum intensity clamped at 0, A = dx dy + dy dz + dz dx of the box)
+// over every k in [f, l), in float with every operation rounded separately (no
+// contraction); a non-finite C never wins; ties go to the least |c_L - c_R|, then the
+// least k. Ranges deeper than the cost depth (root = 1)
+// take the radix split, which bounds the height. Node numbering and parent links are those
+// of topology_kernel, so refit_kernel finishes the hierarchy unchanged.
+//
+// Boxes and maxima are min / max reductions, exact in any order, so parallel scans give
+// the same prefix and suffix aggregates at every k as a serial sweep, and the same costs
+// bit for bit. A range of up to 32 lights: one warp builds its whole subtree, a light per
+// lane; up to 256: one warp, a run of 8 lights per lane; larger ones: tiles of 1024
+// lights, one block per tile and a run of 4 lights per thread. tile_agg_kernel reduces each tile, and the last tile of a
+// range to finish scans the range's tile aggregates; tile_cost_kernel evaluates every
+// split in its tile, and the last tile of a range to finish picks the range's split.
+
+constexpr int kSplitThreads = 256;  // block size of every split kernel
+constexpr int kTileRun = 4;         // lights per thread in a tile
+constexpr uint32_t kSegTile = kSplitThreads * kTileRun;
+constexpr int kMidRun = 8;          // lights per lane for ranges of 33..256 lights
+constexpr uint32_t kSmallMax = 32, kMidMax = 32 * kMidRun;
+constexpr uint32_t kNoSplit = 0xFFFFFFFFu;
+
+struct Seg {
+    uint32_t node, f, l, depth;
+};
+
+struct Agg {  // box and maximum intensity of a set of lights
+    float lo[3], hi[3], m;
+};
+
+struct __align__(16) AggRec {  // (lo xyz, m), (hi xyz, 0)
+    float4 a, b;
+};
+
+struct Best {  // a candidate split, ordered by (c, d, k)
+    float c;
+    uint32_t d, k;
+};
+
+// The next level's range lists, filled by commit_split. Small ranges fill their list from
+// the front, ranges below the cost depth from the back (radix_end[-1], radix_end[-2], ...):
+// the ranges of a level are disjoint, so together they number at most n / 2.
+struct SplitOut {
+    hrr_node *nodes;
+    uint32_t *leaf_parent, *int_parent;
+    uint32_t cost_depth;
+    Seg *small, *radix_end, *mid, *big;
+    uint32_t *big_t0;                // first tile of each big range (increasing)
+    uint32_t *counts;                // [0] small, [1] mid, [2] radix
+    unsigned long long *big_count;   // (big ranges << 32) | tiles
+};
+
+__device__ __forceinline__ Agg agg_empty() {
+    Agg a;
+    for (int c = 0; c < 3; ++c) {
+        a.lo[c] = __int_as_float(0x7f800000);
+        a.hi[c] = -__int_as_float(0x7f800000);
+    }
+    a.m = -__int_as_float(0x7f800000);
+    return a;
+}
+__device__ __forceinline__ Agg agg_of(float4 p) {
+    Agg a;
+    a.lo[0] = a.hi[0] = p.x;
+    a.lo[1] = a.hi[1] = p.y;
+    a.lo[2] = a.hi[2] = p.z;
+    a.m = p.w;
+    return a;
+}
+__device__ __forceinline__ Agg agg_join(const Agg &a, const Agg &b) {
+    Agg r;
+    for (int c = 0; c < 3; ++c) {
+        r.lo[c] = fminf(a.lo[c], b.lo[c]);
+        r.hi[c] = fmaxf(a.hi[c], b.hi[c]);
+    }
+    r.m = fmaxf(a.m, b.m);
+    return r;
+}
+__device__ __forceinline__ Agg agg_shfl(const Agg &a, int delta, bool up) {
+    Agg r;
+    for (int c = 0; c < 3; ++c) {
+        r.lo[c] = up ? __shfl_up_sync(0xFFFFFFFFu, a.lo[c], delta) : __shfl_down_sync(0xFFFFFFFFu, a.lo[c], delta);
+        r.hi[c] = up ? __shfl_up_sync(0xFFFFFFFFu, a.hi[c], delta) : __shfl_down_sync(0xFFFFFFFFu, a.hi[c], delta);
+    }
+    r.m = up ? __shfl_up_sync(0xFFFFFFFFu, a.m, delta) : __shfl_down_sync(0xFFFFFFFFu, a.m, delta);
+    return r;
+}
+__device__ __forceinline__ AggRec agg_pack(const Agg &a) {
+    return {make_float4(a.lo[0], a.lo[1], a.lo[2], a.m), make_float4(a.hi[0], a.hi[1], a.hi[2], 0.f)};
+}
+__device__ __forceinline__ Agg agg_unpack(float4 x, float4 y) {
+    Agg a;
+    a.lo[0] = x.x; a.lo[1] = x.y; a.lo[2] = x.z; a.m = x.w;
+    a.hi[0] = y.x; a.hi[1] = y.y; a.hi[2] = y.z;
+    return a;
+}
+// Written by other blocks of the running kernel: read past L1.
+__device__ __forceinline__ Agg agg_load_cg(const AggRec *r) { return agg_unpack(__ldcg(&r->a), __ldcg(&r->b)); }
+
+__device__ __forceinline__ float half_area(const Agg &a) {
+    const float dx = __fsub_rn(a.hi[0], a.lo[0]), dy = __fsub_rn(a.hi[1], a.lo[1]), dz = __fsub_rn(a.hi[2], a.lo[2]);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx));
+}
+
+// C(k) for children of cl and cr lights
+__device__ __forceinline__ float split_cost(const Agg &L, const Agg &R, uint32_t cl, uint32_t cr) {
+    const float ml = fmaxf(L.m, 0.f), mr = fmaxf(R.m, 0.f);
+    return __fadd_rn(__fmul_rn(__fmul_rn(ml, __fadd_rn(half_area(L), 1e-4f)), __uint2float_rn(cl)),
+                     __fmul_rn(__fmul_rn(mr, __fadd_rn(half_area(R), 1e-4f)), __uint2float_rn(cr)));
+}
+
+__device__ __forceinline__ Best best_none() { return {__int_as_float(0x7f800000), kNoSplit, kNoSplit}; }
+// o < b in (cost, |c_L - c_R|, k) order; a NaN cost never wins
+__device__ __forceinline__ void best_take(Best &b, const Best &o) {
+    if (o.c < b.c || (o.c == b.c && (o.d < b.d || (o.d == b.d && o.k < b.k)))) b = o;
+}
+__device__ __forceinline__ Best warp_best(Best b) {  // the warp's best, in lane 0
+    for (int d = 16; d > 0; d >>= 1) {
+        const Best o = {__shfl_down_sync(0xFFFFFFFFu, b.c, d), __shfl_down_sync(0xFFFFFFFFu, b.d, d),
+                        __shfl_down_sync(0xFFFFFFFFu, b.k, d)};
+        best_take(b, o);
+    }
+    return b;
+}
+// The block's best, in thread 0; sh holds one entry per warp.
+__device__ __forceinline__ Best block_best(Best b, Best *sh) {
+    b = warp_best(b);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < kSplitThreads / 32; ++w) best_take(b, sh[w]);
+    __syncthreads();
+    return b;
+}
+
+// Exclusive scans over the lanes of a warp: the aggregates of lanes [0, lane) and (lane, 31].
+__device__ __forceinline__ void warp_scans(const Agg &x, Agg &before, Agg &after) {
+    const int lane = threadIdx.x & 31;
+    Agg pre = x, suf = x;
+    for (int d = 1; d < 32; d <<= 1) {
+        const Agg u = agg_shfl(pre, d, true), v = agg_shfl(suf, d, false);
+        if (lane >= d) pre = agg_join(pre, u);
+        if (lane + d < 32) suf = agg_join(suf, v);
+    }
+    before = agg_shfl(pre, 1, true);
+    after = agg_shfl(suf, 1, false);
+    if (lane == 0) before = agg_empty();
+    if (lane == 31) after = agg_empty();
+}
+
+// Exclusive scans over the threads of a block, and the block's total; sh holds one entry
+// per warp.
+__device__ __forceinline__ void block_scans(const Agg &x, Agg &before, Agg &after, Agg &total, Agg *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    Agg wb, wa;
+    warp_scans(x, wb, wa);
+    if (lane == 31) sh[w] = agg_join(wb, x);
+    __syncthreads();
+    Agg bb = agg_empty(), ba = agg_empty();
+    total = agg_empty();
+    for (int v = 0; v < kSplitThreads / 32; ++v) {
+        const Agg s = sh[v];
+        if (v < w) bb = agg_join(bb, s);
+        if (v > w) ba = agg_join(ba, s);
+        total = agg_join(total, s);
+    }
+    before = agg_join(bb, wb);
+    after = agg_join(wa, ba);
+    __syncthreads();
+}
+
+// The lights [a, min(a + R, end)) of a thread's run; returns their count.
+template <int R>
+__device__ __forceinline__ uint32_t load_run(const float4 *__restrict__ spos, uint32_t a, uint32_t end, float4 (&p)[R]) {
+    const uint32_t cnt = a < end ? min((uint32_t)R, end - a) : 0u;
+#pragma unroll
+    for (int i = 0; i < R; ++i) p[i] = (uint32_t)i < cnt ? spos[a + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    return cnt;
+}
+template <int R>
+__device__ __forceinline__ Agg run_agg(const float4 (&p)[R], uint32_t cnt) {
+    Agg x = agg_empty();
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+        if ((uint32_t)i < cnt) x = agg_join(x, agg_of(p[i]));
+    return x;
+}
+// Every split k = a + i (k < l) of a run, given the aggregates of [f, a) and of the lights
+// of [f, l] after the run.
+template <int R>
+__device__ __forceinline__ void run_best(const float4 (&p)[R], uint32_t cnt, uint32_t a, const Agg &before,
+                                         const Agg &after, uint32_t f, uint32_t l, Best &b) {
+    Agg suf[R + 1];  // suf[i]: lights a + i .. of the run, then the rest of the range
+    suf[R] = after;
+#pragma unroll
+    for (int i = R - 1; i >= 0; --i) suf[i] = (uint32_t)i < cnt ? agg_join(agg_of(p[i]), suf[i + 1]) : suf[i + 1];
+    Agg pre = before;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        if ((uint32_t)i < cnt) {
+            pre = agg_join(pre, agg_of(p[i]));
+            const uint32_t k = a + i;
+            if (k < l) {
+                const uint32_t cl = k - f + 1, cr = l - k;
+                best_take(b, {split_cost(pre, suf[i + 1], cl, cr), cl > cr ? cl - cr : cr - cl, k});
+            }
+        }
+    }
+}
+
+// Radix split of [f, l]: the last k whose ordering key (Morton key, position) has a 0 at
+// the highest bit where the keys of f and l differ (binary search; the digit is sorted).
+__device__ uint32_t radix_split(const uint64_t *__restrict__ keys, uint32_t f, uint32_t l) {
+    const uint64_t kf = keys[f], kl = keys[l];
+    uint32_t lo = f, hi = l;  // digit(lo) = 0, digit(hi) = 1
+    if (kf != kl) {
+        const int bit = 63 - __clzll((long long)(kf ^ kl));
+        while (hi - lo > 1) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if ((keys[mid] >> bit) & 1ull) hi = mid; else lo = mid;
+        }
+    } else {
+        const int bit = 31 - __clz(f ^ l);
+        while (hi - lo > 1) {
+            const uint32_t mid = lo + (hi - lo) / 2;
+            if ((mid >> bit) & 1u) hi = mid; else lo = mid;
+        }
+    }
+    return lo;
+}
+
+// Record the split s of range g: the node's record and its children's parent links.
+__device__ __forceinline__ void record_split(const Seg &g, uint32_t s, const SplitOut &o) {
+    o.nodes[g.node].split = s;
+    o.nodes[g.node].other_end = g.node == g.f ? g.l : g.f;
+    const uint32_t code = g.node << 1;
+    if (s == g.f) o.leaf_parent[s] = code; else o.int_parent[s] = code;
+    if (s + 1 == g.l) o.leaf_parent[s + 1] = code | 1u; else o.int_parent[s + 1] = code | 1u;
+}
+
+// Record the split of range g and queue its internal children for the next level.
+__device__ void commit_split(const Seg &g, uint32_t s, const SplitOut &o) {
+    if (s == kNoSplit) s = g.f;  // no finite cost: non-finite lights, which fail the build
+    record_split(g, s, o);
+    const Seg kids[2] = {{s, g.f, s, g.depth + 1}, {s + 1, s + 1, g.l, g.depth + 1}};
+    for (int c = 0; c < 2; ++c) {
+        const Seg &k = kids[c];
+        if (k.f == k.l) continue;
+        const uint32_t m = k.l - k.f + 1;
+        if (k.depth > o.cost_depth) {
+            o.radix_end[-1 - (int64_t)atomicAdd(&o.counts[2], 1u)] = k;
+        } else if (m <= kSmallMax) {
+            o.small[atomicAdd(&o.counts[0], 1u)] = k;
+        } else if (m <= kMidMax) {
+            o.mid[atomicAdd(&o.counts[1], 1u)] = k;
+        } else {
+            const unsigned long long old = atomicAdd(o.big_count, (1ull << 32) | ((m + kSegTile - 1) / kSegTile));
+            const uint32_t i = (uint32_t)(old >> 32);
+            o.big[i] = k;
+            o.big_t0[i] = (uint32_t)old;
+        }
+    }
+}
+
+// Ranges below the cost depth: one thread each.
+__global__ void __launch_bounds__(kSplitThreads) split_radix_kernel(const Seg *__restrict__ segs, uint32_t n_segs,
+                                                                    const uint64_t *__restrict__ keys, SplitOut o) {
+    const uint32_t i = blockIdx.x * kSplitThreads + threadIdx.x;
+    if (i >= n_segs) return;
+    const Seg g = segs[i];
+    commit_split(g, radix_split(keys, g.f, g.l), o);
+}
+
+// Ranges of up to 32 lights: one warp builds the whole subtree, one level of it per
+// iteration. Lane j holds light f0 + j and the range of the level that holds it; scans and
+// the reduction to the range's first lane are segmented by those ranges.
+__global__ void __launch_bounds__(kSplitThreads) subtree_warp_kernel(const Seg *__restrict__ segs, uint32_t n_segs,
+                                                                     const float4 *__restrict__ spos,
+                                                                     const uint64_t *__restrict__ keys, SplitOut o) {
+    const uint32_t w = (blockIdx.x * kSplitThreads + threadIdx.x) >> 5;
+    if (w >= n_segs) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const Seg g0 = segs[w];
+    const uint32_t i = g0.f + (uint32_t)lane;
+    const bool valid = i <= g0.l;
+    const Agg self = valid ? agg_of(spos[i]) : agg_empty();
+    Seg g = valid ? g0 : Seg{i, i, i, 0u};  // lanes past the range: a closed range of their own
+    // a range of at most 32 lights is at most 31 levels deep
+    for (int level = 0; level < 32 && __any_sync(0xFFFFFFFFu, g.l > g.f); ++level) {
+        const int lf = (int)(g.f - g0.f), ll = (int)(g.l - g0.f);  // this lane's range, as lanes
+        Agg pre = self, suf = self;  // inclusive scans within the range
+        for (int d = 1; d < 32; d <<= 1) {
+            const Agg u = agg_shfl(pre, d, true), v = agg_shfl(suf, d, false);
+            if (lane - d >= lf) pre = agg_join(pre, u);
+            if (lane + d <= ll) suf = agg_join(suf, v);
+        }
+        const Agg right = agg_shfl(suf, 1, false);  // [i + 1, l] for i < l
+        Best b = best_none();
+        if (lane < ll) {
+            const uint32_t cl = i - g.f + 1, cr = g.l - i;
+            b = {split_cost(pre, right, cl, cr), cl > cr ? cl - cr : cr - cl, i};
+        }
+        for (int d = 1; d < 32; d <<= 1) {  // the range's best split, in its first lane
+            const Best ob = {__shfl_down_sync(0xFFFFFFFFu, b.c, d), __shfl_down_sync(0xFFFFFFFFu, b.d, d),
+                             __shfl_down_sync(0xFFFFFFFFu, b.k, d)};
+            if (lane + d <= ll) best_take(b, ob);
+        }
+        uint32_t s = 0;
+        if (lane == lf && ll > lf) {
+            s = g.depth <= o.cost_depth ? (b.k == kNoSplit ? g.f : b.k) : radix_split(keys, g.f, g.l);
+            record_split(g, s, o);
+        }
+        s = __shfl_sync(0xFFFFFFFFu, s, lf);
+        if (ll > lf) g = i <= s ? Seg{s, g.f, s, g.depth + 1} : Seg{s + 1, s + 1, g.l, g.depth + 1};
+    }
+}
+
+// Ranges of up to 32 R lights: one warp each, a run of R lights per lane.
+template <int R>
+__global__ void __launch_bounds__(kSplitThreads) split_warp_kernel(const Seg *__restrict__ segs, uint32_t n_segs,
+                                                                   const float4 *__restrict__ spos, SplitOut o) {
+    const uint32_t w = (blockIdx.x * kSplitThreads + threadIdx.x) >> 5;
+    if (w >= n_segs) return;  // warp-uniform
+    const int lane = threadIdx.x & 31;
+    const Seg g = segs[w];
+    const uint32_t a = g.f + (uint32_t)lane * R;
+    float4 p[R];
+    const uint32_t cnt = load_run<R>(spos, a, g.l + 1, p);
+    Agg before, after;
+    warp_scans(run_agg<R>(p, cnt), before, after);
+    Best b = best_none();
+    run_best<R>(p, cnt, a, before, after, g.f, g.l, b);
+    b = warp_best(b);
+    if (lane == 0) commit_split(g, b.k, o);
+}
+
+// The big range holding tile t: the last i with big_t0[i] <= t.
+__device__ __forceinline__ uint32_t range_of_tile(const uint32_t *__restrict__ big_t0, uint32_t n_big, uint32_t t) {
+    uint32_t lo = 0, hi = n_big;
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (big_t0[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+struct TileSite {  // a tile of a big range
+    Seg g;
+    uint32_t i, t0, nt, start, end;  // range index, first tile, tiles, lights [start, end)
+};
+
+__device__ __forceinline__ TileSite tile_site(const Seg *__restrict__ big, const uint32_t *__restrict__ big_t0,
+                                              uint32_t n_big, uint32_t *s_i) {
+    if (threadIdx.x == 0) *s_i = range_of_tile(big_t0, n_big, blockIdx.x);
+    __syncthreads();
+    TileSite s;
+    s.i = *s_i;
+    s.g = big[s.i];
+    s.t0 = big_t0[s.i];
+    s.nt = (s.g.l - s.g.f + 1 + kSegTile - 1) / kSegTile;
+    s.start = s.g.f + (blockIdx.x - s.t0) * kSegTile;
+    s.end = s.g.l + 1 - s.start > kSegTile ? s.start + kSegTile : s.g.l + 1;
+    return s;
+}
+
+// Tile aggregates of ranges of more than one tile; the last tile of a range to finish
+// writes, for every tile, the aggregates of the range's tiles before it and after it.
+__global__ void __launch_bounds__(kSplitThreads) tile_agg_kernel(
+    const Seg *__restrict__ big, const uint32_t *__restrict__ big_t0, uint32_t n_big, const float4 *__restrict__ spos,
+    AggRec *tile_agg, AggRec *tile_pre, AggRec *tile_suf, uint32_t *done) {
+    __shared__ Agg sh[kSplitThreads / 32];
+    __shared__ uint32_t s_i;
+    __shared__ int s_last;
+    const TileSite s = tile_site(big, big_t0, n_big, &s_i);
+    if (s.nt == 1) return;  // block-uniform
+    float4 p[kTileRun];
+    const uint32_t cnt = load_run<kTileRun>(spos, s.start + threadIdx.x * kTileRun, s.end, p);
+    Agg before, after, total;
+    block_scans(run_agg<kTileRun>(p, cnt), before, after, total, sh);
+    if (threadIdx.x == 0) {
+        tile_agg[blockIdx.x] = agg_pack(total);
+        __threadfence();
+        s_last = atomicAdd(&done[s.i], 1u) == s.nt - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    Agg carry = agg_empty();
+    for (uint32_t base = 0; base < s.nt; base += kSplitThreads) {  // tiles before
+        const uint32_t j = base + threadIdx.x;
+        const Agg y = j < s.nt ? agg_load_cg(&tile_agg[s.t0 + j]) : agg_empty();
+        block_scans(y, before, after, total, sh);
+        if (j < s.nt) tile_pre[s.t0 + j] = agg_pack(agg_join(carry, before));
+        carry = agg_join(carry, total);
+    }
+    carry = agg_empty();
+    for (uint32_t base = (s.nt - 1) / kSplitThreads * kSplitThreads;; base -= kSplitThreads) {  // tiles after
+        const uint32_t j = base + threadIdx.x;
+        const Agg y = j < s.nt ? agg_load_cg(&tile_agg[s.t0 + j]) : agg_empty();
+        block_scans(y, before, after, total, sh);
+        if (j < s.nt) tile_suf[s.t0 + j] = agg_pack(agg_join(after, carry));
+        carry = agg_join(carry, total);
+        if (base == 0) break;
+    }
+    if (threadIdx.x == 0) done[s.i] = 0;
+}
+
+// Every split in a tile of a big range; a range of one tile records its split here, else
+// the last tile of the range to finish reduces the tiles' best splits and records it.
+__global__ void __launch_bounds__(kSplitThreads) tile_cost_kernel(
+    const Seg *__restrict__ big, const uint32_t *__restrict__ big_t0, uint32_t n_big, const float4 *__restrict__ spos,
+    const AggRec *__restrict__ tile_pre, const AggRec *__restrict__ tile_suf, Best *tile_best, uint32_t *done,
+    SplitOut o) {
+    __shared__ Agg sh[kSplitThreads / 32];
+    __shared__ Best shb[kSplitThreads / 32];
+    __shared__ uint32_t s_i;
+    __shared__ int s_last;
+    const TileSite s = tile_site(big, big_t0, n_big, &s_i);
+    const uint32_t a = s.start + threadIdx.x * kTileRun;
+    float4 p[kTileRun];
+    const uint32_t cnt = load_run<kTileRun>(spos, a, s.end, p);
+    Agg before, after, total;
+    block_scans(run_agg<kTileRun>(p, cnt), before, after, total, sh);
+    if (s.nt > 1) {
+        const AggRec pre = tile_pre[blockIdx.x], suf = tile_suf[blockIdx.x];
+        before = agg_join(agg_unpack(pre.a, pre.b), before);
+        after = agg_join(after, agg_unpack(suf.a, suf.b));
+    }
+    Best b = best_none();
+    run_best<kTileRun>(p, cnt, a, before, after, s.g.f, s.g.l, b);
+    b = block_best(b, shb);
+    if (s.nt == 1) {  // block-uniform
+        if (threadIdx.x == 0) commit_split(s.g, b.k, o);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        tile_best[blockIdx.x] = b;
+        __threadfence();
+        s_last = atomicAdd(&done[s.i], 1u) == s.nt - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    Best r = best_none();
+    for (uint32_t j = threadIdx.x; j < s.nt; j += kSplitThreads) {
+        const Best *q = &tile_best[s.t0 + j];
+        best_take(r, {__ldcg(&q->c), __ldcg(&q->d), __ldcg(&q->k)});
+    }
+    r = block_best(r, shb);
+    if (threadIdx.x == 0) {
+        done[s.i] = 0;
+        commit_split(s.g, r.k, o);
+    }
+}
+
 }  // namespace
 
-int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out) {
+namespace {
+
+// The cost-driven topology for n >= 2 sorted lights: writes split / other_end of every
+// record and the parent links, level by level (one host round trip per level).
+int cost_topology(hrr_ctx *ctx, const float4 *spos, const uint64_t *keys, uint32_t n, uint32_t cost_depth,
+                  hrr_node *nodes, uint32_t *leaf_parent, uint32_t *int_parent, cudaStream_t st) {
+    const size_t cap_s = (size_t)n / 2 + 1;                    // ranges of >= 2 lights in a level
+    const size_t cap_m = (size_t)n / (kSmallMax + 1) + 1;      // ... of > 32
+    const size_t cap_b = (size_t)n / (kMidMax + 1) + 1;        // ... of > 256
+    const size_t cap_t = (size_t)n / kSegTile + cap_b + 1;     // tiles of those
+    auto rup = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t bytes = 2 * (rup(sizeof(Seg) * cap_s) + rup(sizeof(Seg) * cap_m) + rup(sizeof(Seg) * cap_b) +
+                              rup(sizeof(uint32_t) * cap_b)) +
+                         3 * rup(sizeof(AggRec) * cap_t) + rup(sizeof(Best) * cap_t) + rup(sizeof(uint32_t) * cap_b) +
+                         256;
+    char *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
+    if (e != cudaSuccess) return hrr_cuda_fail(ctx, e, "topology scratch");
+    struct Lists {
+        Seg *small, *radix_end, *mid, *big;
+        uint32_t *big_t0;
+    } in, out;
+    char *p = scratch;
+    for (Lists *L : {&in, &out}) {
+        L->small = carve<Seg>(p, cap_s);
+        L->radix_end = L->small + cap_s;
+        L->mid = carve<Seg>(p, cap_m);
+        L->big = carve<Seg>(p, cap_b);
+        L->big_t0 = carve<uint32_t>(p, cap_b);
+    }
+    AggRec *tile_agg = carve<AggRec>(p, cap_t), *tile_pre = carve<AggRec>(p, cap_t), *tile_suf = carve<AggRec>(p, cap_t);
+    Best *tile_best = carve<Best>(p, cap_t);
+    uint32_t *done = carve<uint32_t>(p, cap_b);
+    uint32_t *counts = carve<uint32_t>(p, 6);  // small, mid, radix, pad, big (64-bit)
+    unsigned long long *big_count = reinterpret_cast<unsigned long long *>(counts + 4);
+
+    const Seg root{0u, 0u, n - 1, 1u};
+    uint32_t ns = 0, nm = 0, nr = 0, nb = 0, ntiles = 0;
+    Seg *root_list;
+    if (n <= kSmallMax) { ns = 1; root_list = in.small; }
+    else if (n <= kMidMax) { nm = 1; root_list = in.mid; }
+    else { nb = 1; ntiles = (uint32_t)(((size_t)n + kSegTile - 1) / kSegTile); root_list = in.big; }
+    e = cudaMemcpyAsync(root_list, &root, sizeof(Seg), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(in.big_t0, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, sizeof(uint32_t) * cap_b, st);
+    uint32_t *host = reinterpret_cast<uint32_t *>(&ctx->host_counters[5]);  // 6 words of pinned memory
+    int rc = HRR_OK;
+    for (int level = 0; e == cudaSuccess && ns + nm + nr + nb > 0; ++level) {
+        if (level > (int)cost_depth + 100) {  // the radix split bounds the height
+            rc = hrr_fail(ctx, HRR_ERR_DEVICE, "topology build did not terminate");
+            break;
+        }
+        if ((e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * 6, st)) != cudaSuccess) break;
+        const SplitOut o{nodes, leaf_parent, int_parent, cost_depth, out.small, out.radix_end, out.mid, out.big,
+                         out.big_t0, counts, big_count};
+        if (nr) {
+            split_radix_kernel<<<(nr + kSplitThreads - 1) / kSplitThreads, kSplitThreads, 0, st>>>(in.radix_end - nr,
+                                                                                               nr, keys, o);
+            ++ctx->launches;
+        }
+        if (ns) {
+            subtree_warp_kernel<<<(unsigned)(((size_t)ns * 32 + kSplitThreads - 1) / kSplitThreads), kSplitThreads, 0,
+                                  st>>>(in.small, ns, spos, keys, o);
+            ++ctx->launches;
+        }
+        if (nm) {
+            split_warp_kernel<kMidRun><<<(unsigned)(((size_t)nm * 32 + kSplitThreads - 1) / kSplitThreads), kSplitThreads,
+                                         0, st>>>(in.mid, nm, spos, o);
+            ++ctx->launches;
+        }
+        if (nb) {
+            if (ntiles > nb) {  // some range spans several tiles
+                tile_agg_kernel<<<ntiles, kSplitThreads, 0, st>>>(in.big, in.big_t0, nb, spos, tile_agg, tile_pre,
+                                                                  tile_suf, done);
+                ++ctx->launches;
+            }
+            tile_cost_kernel<<<ntiles, kSplitThreads, 0, st>>>(in.big, in.big_t0, nb, spos, tile_pre, tile_suf,
+                                                               tile_best, done, o);
+            ++ctx->launches;
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(host, counts, sizeof(uint32_t) * 6, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
+        ns = host[0];
+        nm = host[1];
+        nr = host[2];
+        const unsigned long long bc = (unsigned long long)host[4] | ((unsigned long long)host[5] << 32);
+        nb = (uint32_t)(bc >> 32);
+        ntiles = (uint32_t)bc;
+        std::swap(in, out);
+    }
+    cudaFreeAsync(scratch, st);
+    if (e != cudaSuccess) return hrr_cuda_fail(ctx, e, "topology build");
+    return rc;
+}
+
+}  // namespace
+
+int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out, int topology, uint32_t cost_depth) {
     cudaStream_t st = ctx->stream;
     hrr_tree *tree = new (std::nothrow) hrr_tree();
     if (!tree) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of the tree");
@@ -359,7 +947,7 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
             uint32_t *vin = vals0, *vout = vals1;
             for (int shift = 0; shift < 64; shift += 8) {
                 radix_hist_kernel<<<nblocks, kThreads, 0, st>>>(kin, n, shift, hist, nblocks);
-                exclusive_scan_kernel<<<1, 1024, 0, st>>>(hist, hist_n);
+                exclusive_scan_kernel<<<1, 1024, 0, st>>>(hist, nblocks);
                 radix_scatter_kernel<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n, shift, hist, nblocks);
                 ctx->launches += 3;
                 uint64_t *tk = kin; kin = kout; kout = tk;
@@ -370,10 +958,15 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
             if ((e = cudaMemsetAsync(arrivals, 0, sizeof(uint32_t) * (size_t)n, st)) != cudaSuccess) { rc = hrr_cuda_fail(ctx, e, "memset"); break; }
             if ((e = cudaMemsetAsync(leaf_parent, 0xFF, 2 * ((sizeof(uint32_t) * (size_t)n + 255) & ~size_t(255)), st)) != cudaSuccess) { rc = hrr_cuda_fail(ctx, e, "memset"); break; }
             const unsigned gi = (n - 1 + kThreads - 1) / kThreads;
-            topology_kernel<<<gi, kThreads, 0, st>>>(keys0, n, tree->nodes, leaf_parent, int_parent);
+            if (topology == HRR_TOPOLOGY_COST) {
+                if ((rc = cost_topology(ctx, spos, keys0, n, cost_depth, tree->nodes, leaf_parent, int_parent, st)) != HRR_OK) break;
+            } else {
+                topology_kernel<<<gi, kThreads, 0, st>>>(keys0, n, tree->nodes, leaf_parent, int_parent);
+                ++ctx->launches;
+            }
             refit_kernel<<<g, kThreads, 0, st>>>(spos, n, tree->nodes, leaf_parent, int_parent, arrivals,
                                                  child_height, root_height, flags);
-            ctx->launches += 3;
+            ctx->launches += 2;
             if ((e = cudaGetLastError()) != cudaSuccess) { rc = hrr_cuda_fail(ctx, e, "build kernels"); break; }
             if ((e = cudaMemcpyAsync(&ctx->host_counters[4], root_height, sizeof(uint32_t),
                                      cudaMemcpyDeviceToHost, st)) != cudaSuccess) { rc = hrr_cuda_fail(ctx, e, "height copy"); break; }
@@ -531,7 +1124,6 @@ extern "C" int hrr_build_light_tree_static(hrr_lights L, uint32_t n, hrr_node *d
         }
     } else {
         const uint32_t nblocks = (n + kTile - 1) / kTile;
-        const uint64_t hist_n = 256ull * nblocks;
         if (e == cudaSuccess) e = cudaMemsetAsync(arrivals, 0, sizeof(uint32_t) * (size_t)n, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(leaf_parent, 0xFF, sizeof(uint32_t) * (size_t)n, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(int_parent, 0xFF, sizeof(uint32_t) * (size_t)n, st);
@@ -542,7 +1134,7 @@ extern "C" int hrr_build_light_tree_static(hrr_lights L, uint32_t n, hrr_node *d
             uint32_t *vin = dev_perm, *vout = vals1;
             for (int shift = 0; shift < 64; shift += 8) {
                 radix_hist_kernel<<<nblocks, kThreads, 0, st>>>(kin, n, shift, hist, nblocks);
-                exclusive_scan_kernel<<<1, 1024, 0, st>>>(hist, hist_n);
+                exclusive_scan_kernel<<<1, 1024, 0, st>>>(hist, nblocks);
                 radix_scatter_kernel<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n, shift, hist, nblocks);
                 uint64_t *tk = kin; kin = kout; kout = tk;
                 uint32_t *tv = vin; vin = vout; vout = tv;

@@ -137,7 +137,8 @@ cudaError_t hrr_refit_enqueue(hrr_tree *tree, const hrr_lights &lights, void *sc
                               cudaStream_t st);
 
 // Entry points implemented per translation unit
-int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &lights, uint32_t n, hrr_tree **out);
+int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &lights, uint32_t n, hrr_tree **out,
+                   int topology = HRR_TOPOLOGY_RADIX, uint32_t cost_depth = 48);
 int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &eyes, uint32_t n_eyes, const hrr_tree *tree,
                   float tau, const hrr_cull_opts &opts, uint32_t *pairs, uint64_t cap,
                   uint64_t *out_count);

@@ -31,7 +31,7 @@ def _check_tree(t):
 
 def test_dark_lights_split_in_the_middle():
     # zero intensities: every candidate costs exactly 0, ties go to the middle, so the tree
-    # is perfectly balanced (2048 lights also exercise the candidate stride q = 2)
+    # is perfectly balanced
     for n in (8, 16, 64, 2048):
         rng = np.random.default_rng(n)
         pos = rng.random((n, 3)).astype(np.float32)
@@ -52,23 +52,23 @@ def test_two_clusters_are_separated_at_the_root():
 
 
 def _rule(pos, inten, f, l):
-    """The split rule restated in float64 numpy: candidates every q-th split, cost, ties."""
-    m = l - f + 1
-    q = -(-m // 1024)
-    P = pos[f:l + 1].astype(np.float64)
-    I = inten[f:l + 1].astype(np.float64)
+    """The split rule restated in float32 numpy (every operation rounded to float32): every
+    split, cost, ties."""
+    f32 = np.float32
+    P = pos[f:l + 1].astype(f32)
+    I = inten[f:l + 1].astype(f32)
+    eps = f32(1e-4)
     best = None
     for k in range(f, l):
-        if (k - f + 1) % q:
-            continue
         L, R = P[: k - f + 1], P[k - f + 1:]
         dl, dr = L.max(0) - L.min(0), R.max(0) - R.min(0)
-        al = dl[0] * dl[1] + dl[1] * dl[2] + dl[2] * dl[0]
-        ar = dr[0] * dr[1] + dr[1] * dr[2] + dr[2] * dr[0]
-        ml, mr = max(I[: k - f + 1].max(), 0.0), max(I[k - f + 1:].max(), 0.0)
+        al = (dl[0] * dl[1] + dl[1] * dl[2]) + dl[2] * dl[0]
+        ar = (dr[0] * dr[1] + dr[1] * dr[2]) + dr[2] * dr[0]
+        ml, mr = max(I[: k - f + 1].max(), f32(0)), max(I[k - f + 1:].max(), f32(0))
         cl, cr = k - f + 1, l - k
-        cost = ml * (al + 1e-4) * cl + mr * (ar + 1e-4) * cr
-        key = (cost, abs(cl - cr), k)
+        cost = (ml * (al + eps)) * f32(cl) + (mr * (ar + eps)) * f32(cr)
+        assert cost.dtype == f32
+        key = (float(cost), abs(cl - cr), k)
         best = key if best is None or key < best else best
     return best[2]
 
@@ -119,3 +119,38 @@ def test_fewer_visits_than_the_radix_tree_on_the_frame_workload():
         t = oracle.Tree(s.light_pos, s.intensity, topology=topo)
         v[topo] = oracle.cull_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)["total_visits"]
     assert v["cost"] < 0.92 * v["radix"]
+
+
+def _radix_rule(keys, f, l):
+    """The radix split restated: the last k whose key has a 0 at the highest bit where the
+    keys of f and l differ; for equal keys, the same on the positions f and l."""
+    kf, kl = int(keys[f]), int(keys[l])
+    if kf != kl:
+        bit = (kf ^ kl).bit_length() - 1
+        digits = [(int(keys[k]) >> bit) & 1 for k in range(f, l + 1)]
+    else:
+        bit = (f ^ l).bit_length() - 1
+        digits = [(k >> bit) & 1 for k in range(f, l + 1)]
+    return f + max(i for i, d in enumerate(digits) if d == 0)
+
+
+@pytest.mark.parametrize("depth", [1, 3, 6])
+def test_cost_depth_hands_over_to_radix_splits(depth):
+    s = synth.scene_frame(width=8, height=8, n_lights=1500, seed=11)
+    t = oracle.Tree(s.light_pos, s.intensity, topology="cost", cost_depth=depth)
+    _check_tree(t)
+    assert t.height <= depth + 96
+    stack, checked = [(0, 1)], 0
+    while stack:
+        k, d = stack.pop()
+        f, l, sp = int(t.first[k]), int(t.last[k]), int(t.split[k])
+        if d <= depth:
+            if d <= 2:
+                assert sp == _rule(t.pos, t.inten, f, l)
+        else:
+            assert sp == _radix_rule(t.key, f, l)
+            checked += 1
+        for cf, cl, cid in ((f, sp, sp), (sp + 1, l, sp + 1)):
+            if cf != cl:
+                stack.append((cid, d + 1))
+    assert checked > 0
