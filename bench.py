@@ -264,10 +264,11 @@ def run_ours(args):
     return result
 
 
-# Algorithmic work of one node visit on the frame workload (derivation in the design doc, sec. 6):
-# 1.963 internal child tests x 27 float ops (bound + cull predicate) + 0.977 range minima x
-# 51 integer ops + 0.774 inherited minima x 2 + 0.037 leaf tests x 17.
-OPS_PER_VISIT = 1.963 * 27 + 0.977 * 51 + 0.774 * 2 + 0.037 * 17
+# Algorithmic work of one node visit on the frame workload with the cost-driven hierarchy
+# (counted with the oracle's traversal over 3,000 evenly spaced eyes): 1.960 internal child
+# tests x 27 float ops (bound + cull predicate) + 0.973 new range minima x 51 integer ops +
+# 0.988 inherited minima x 2 + 0.040 leaf tests x 17. The radix tree's mix gives 105.26.
+OPS_PER_VISIT = 1.960 * 27 + 0.973 * 51 + 0.988 * 2 + 0.040 * 17
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_1920x1080.md")
 TOPOLOGY = "cost"  # hierarchy shape of the benchmarked builds (set from --topology)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
