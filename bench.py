@@ -275,13 +275,18 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
                   for f in ("hrr_cull.cu", "hrr_math.cuh")]
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(files=None) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in files or KERNEL_SOURCES:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def build_source_hash() -> str:
+    """The hierarchy build's source: the cull's traffic depends on the tree it walks."""
+    return kernel_source_hash([os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", "hrr_build.cu")])
 
 
 def profiled_traffic(workload="", topology=None):
@@ -301,6 +306,8 @@ def profiled_traffic(workload="", topology=None):
     if workload and vals.get("workload_eyes") != workload:
         return None
     if vals.get("topology") != (topology or TOPOLOGY):
+        return None
+    if vals.get("build_source_sha256") != build_source_hash():
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -352,8 +359,10 @@ def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk, workload=""):
 
 
 def run_e2e(ctx, s, dev, stream, args, cap):
-    """Same metric through the C ABI with host buffers: pinned host inputs copied in,
-    hierarchy built, eyes culled, accepted pairs and count copied back, every step."""
+    """Same metric through the C ABI with host buffers: pinned host lights copied in and the
+    hierarchy built, then hrr_cull_host reads the eyes from pinned host memory and writes
+    the accepted pairs to pinned host memory (its slices' copies overlap the culling),
+    every step."""
     import numpy as np
     import torch
     import paper_1907_12343_gb300 as hrr
@@ -364,8 +373,6 @@ def run_e2e(ctx, s, dev, stream, args, cap):
     host_e = [torch.from_numpy(np.ascontiguousarray(s.eye_pos[:, k])).pin_memory() for k in range(3)]
     host_e += [torch.from_numpy(s.px.view(np.int16)).pin_memory(), torch.from_numpy(s.py.view(np.int16)).pin_memory()]
     dev_l = [torch.empty_like(h, device=dev) for h in host_l]
-    dev_e = [torch.empty_like(h, device=dev) for h in host_e]
-    pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev)
     host_pairs = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
     h2d = sum(h.numel() * h.element_size() for h in host_l + host_e)
     steps = max(2, min(args.steps, 5))
@@ -374,14 +381,13 @@ def run_e2e(ctx, s, dev, stream, args, cap):
         for k in range(steps + 1):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            for h, d in zip(host_l + host_e, dev_l + dev_e):
+            for h, d in zip(host_l, dev_l):
                 d.copy_(h, non_blocking=True)
             tree = ctx.build_light_tree(*dev_l, topology=TOPOLOGY)
-            st, cnt = ctx.cull(*dev_e[:3], dev_e[3], dev_e[4], tree, float(s.tau), pairs)
+            st, cnt = ctx.cull_host(*host_e, tree, float(s.tau), host_pairs)
             tree.free()
             if st != hrr.HRR_OK:
                 raise RuntimeError(f"cull status {st}")
-            host_pairs[:cnt].copy_(pairs[:cnt], non_blocking=True)
             stream.synchronize()
             dt = time.perf_counter() - t0
             if k > 0:  # first iteration warms the pinned buffers

@@ -155,13 +155,13 @@ int hrr_build_light_tree(hrr_ctx *ctx, hrr_lights lights, uint32_t n_lights, hrr
 
 /* Hierarchy shapes over the same Morton leaf order (so the same accepted set, Sec. 1):
  * RADIX splits every range at the highest differing bit of its end keys (a binary radix
- * tree); COST splits each range down to depth cost_depth (root = 1) where
- *     m_L (A_L + 1e-4) c_L + m_R (A_R + 1e-4) c_R
- * is least (c light count, m maximum intensity clamped at 0, A = dx dy + dy dz + dz dx of
- * the child's box; double, each operation rounded separately; every split a candidate;
- * ties to the most even split, then the smaller one) and takes radix splits below, which
- * bound the height by cost_depth + 96. COST trees take fewer node visits to cull (about
- * 13% on the frame workload) and a few more milliseconds to build. */
+ * tree); COST splits each range down to depth cost_depth (root = 1) where w(L) + w(R) is
+ * least, w(X) = u^2 ((A + 0.1 P) + 1e-4) c sqrt(c) for a child of c lights whose maximum
+ * intensity (clamped at 0) is u times the range's, A = dx dy + dy dz + dz dx and
+ * P = dx + dy + dz of its box (float, each operation rounded separately; every split a
+ * candidate; ties to the most even split, then the smaller one), and takes radix splits
+ * below, which bound the height by cost_depth + 96. COST trees take fewer node visits to
+ * cull (about 15% on the frame workload) and about a millisecond more to build. */
 typedef enum hrr_topology { HRR_TOPOLOGY_RADIX = 0, HRR_TOPOLOGY_COST = 1 } hrr_topology;
 
 typedef struct hrr_build_opts {
@@ -248,6 +248,18 @@ int hrr_cull(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree,
 int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree,
                 float tau, const hrr_cull_opts *opts, uint32_t *dev_pairs, uint64_t cap,
                 uint64_t *out_count);
+/* hrr_cull with host buffers: the eyes are read from host memory (host_eyes: host SoA,
+ * n_eyes entries each) and the accepted pairs written to host memory (host_pairs: 2 * cap
+ * uint32), as (eye index, original light id) with the same set as hrr_cull_ex gives for the
+ * same eyes and options. Pinned host memory lets the copies overlap the culling: the eyes
+ * are culled in up to four slices in order, each slice's eyes are copied in ahead of it and
+ * its pairs copied out while the next slice runs. The context keeps device copies of the
+ * eyes and pairs (grown on demand, freed by hrr_destroy) and a copy stream. Statuses as in
+ * hrr_cull_ex (HRR_ERR_OVERFLOW: *out_count holds the need, the first cap pairs of the
+ * buffer are written). opts may be NULL; its eye_visits, if set, is device memory.
+ * Synchronous. */
+int hrr_cull_host(hrr_ctx *ctx, hrr_eyes host_eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
+                  const hrr_cull_opts *opts, uint32_t *host_pairs, uint64_t cap, uint64_t *out_count);
 /* Statistics of the last hrr_cull/hrr_cull_ex on this context: total internal-node
  * visits and accepted pairs (both exact, computed on the device). */
 int hrr_last_cull_stats(const hrr_ctx *ctx, uint64_t *visits, uint64_t *accepted);

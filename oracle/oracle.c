@@ -23,6 +23,7 @@
 #include "oracle.h"
 
 #include <fenv.h>
+#include <float.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -477,17 +478,29 @@ static void boxes_from_leaves(or_tree *t)
     }
 }
 
+/* Cost of one child in the cost-driven split: m its maximum intensity clamped at 0, inv
+ * the reciprocal of the range's clamped maximum (0 for a dark range), (dx, dy, dz) its box
+ * extent and c its light count. With u = m inv (in [0, 1]), A = dx dy + dy dz + dz dx and
+ * P = dx + dy + dz, the cost is u^2 ((A + 0.1 P) + 1e-4) c sqrt(c), in float with every
+ * operation rounded separately, in this order. */
+static float child_cost(float m, float inv, float dx, float dy, float dz, float c)
+{
+    float u = m * inv;
+    float a = dx * dy + dy * dz + dz * dx;
+    float p = dx + dy + dz;
+    float g = (a + 0.1f * p) + 1e-4f;
+    return ((u * u) * g) * (c * sqrtf(c));
+}
+
 /* Cost-driven split of the range [f, l] (l > f) over the same leaf order: among the
  * candidate splits k (children [f, k] and [k+1, l]), the one minimising
- *     C(k) = m_L (A_L + 1e-4) c_L + m_R (A_R + 1e-4) c_R,
- * with c the child's light count, m its maximum intensity clamped at 0 and A half the
- * surface area of its box (dx dy + dy dz + dz dx), all in float, each operation rounded
- * separately, in this order (the counts converted to float with rounding to nearest). A
- * node is visited about in proportion to its count times its maximum intensity over its
- * squared distance, so lowering C lowers the expected visits. Every k in [f, l) is a
- * candidate; a non-finite C never wins. Ties go to the split nearest the middle (the least
- * |c_L - c_R|), then to the smaller k; with no finite C the split is f. suf holds 7 floats
- * per leaf of scratch. */
+ * C(k) = child_cost(left) + child_cost(right). A node is visited about in proportion to
+ * its count times its maximum intensity over its squared distance; the weights (intensity
+ * squared, count to the 1.5, a perimeter term beside the half area) were chosen by the
+ * visits they save on several synthetic scenes. Every k in [f, l) is a candidate; a
+ * non-finite C never wins. Ties go to the split nearest the middle (the least
+ * |c_L - c_R|), then to the smaller k; with no finite C the split is f. The counts are
+ * converted to float with rounding to nearest. suf holds 7 floats per leaf of scratch. */
 static uint32_t cost_split(const or_tree *t, uint32_t f, uint32_t l, float *suf)
 {
     /* suffix boxes and maxima: suf[7 * (i - f)] = lo xyz, hi xyz, max intensity of [i, l] */
@@ -524,11 +537,11 @@ static uint32_t cost_split(const or_tree *t, uint32_t f, uint32_t l, float *suf)
         const float *r = &suf[7 * (uint64_t)(k + 1 - f)];
         float dxl = hi[0] - lo[0], dyl = hi[1] - lo[1], dzl = hi[2] - lo[2];
         float dxr = r[3] - r[0], dyr = r[4] - r[1], dzr = r[5] - r[2];
-        float al = dxl * dyl + dyl * dzl + dzl * dxl;
-        float ar = dxr * dyr + dyr * dzr + dzr * dxr;
         float ml = fmaxf(m, 0.0f), mr = fmaxf(r[6], 0.0f);
+        float mx = fmaxf(ml, mr);
+        float inv = mx > 0.0f ? 1.0f / fmaxf(mx, FLT_MIN) : 0.0f;
         float cl = (float)(k - f + 1), cr = (float)(l - k);
-        float cost = ml * (al + 1e-4f) * cl + mr * (ar + 1e-4f) * cr;
+        float cost = child_cost(ml, inv, dxl, dyl, dzl, cl) + child_cost(mr, inv, dxr, dyr, dzr, cr);
         int64_t dist = (int64_t)(k - f + 1) - (int64_t)(l - k);
         if (dist < 0)
             dist = -dist;

@@ -136,6 +136,8 @@ _SIGS = {
     "hrr_cull": (_i32, [_P, hrr_eyes, _u32, _P, _f32, _P, _u64, C.POINTER(_u64)]),
     "hrr_cull_ex": (_i32, [_P, hrr_eyes, _u32, _P, _f32, C.POINTER(hrr_cull_opts), _P, _u64,
                            C.POINTER(_u64)]),
+    "hrr_cull_host": (_i32, [_P, hrr_eyes, _u32, _P, _f32, C.POINTER(hrr_cull_opts), _P, _u64,
+                             C.POINTER(_u64)]),
     "hrr_last_cull_stats": (_i32, [_P, C.POINTER(_u64), C.POINTER(_u64)]),
     "hrr_range_min": (_i32, [_P, _P, _P, _P, _P, _P, _u64, _i32]),
     "hrr_build_light_tree_static": (_i32, [hrr_lights, _u32, _P, _P, C.POINTER(_u32), _P,
@@ -283,6 +285,24 @@ class Context:
                              shift_offset, int(t.get("blocks_per_sm", 0)), int(sample_index))
         st = hrr_cull_ex(self.handle, E, n, tree.handle, float(tau), C.byref(opts),
                          _ptr(pairs) if cap else None, cap, C.byref(cnt))
+        if st not in (HRR_OK, HRR_ERR_OVERFLOW):
+            self.check(st)
+        return st, int(cnt.value)
+
+    def cull_host(self, x, y, z, px, py, tree: "Tree", tau: float, pairs, rangemin_variant: int = 0,
+                  shift_offset: int = 0, tuning=None, sample_index: int = 0):
+        """``cull`` with host buffers: the eye arrays and ``pairs`` (shape (cap, 2), uint32 or
+        int32) live in host memory (pinned memory lets the copies overlap the culling);
+        returns (status, count)."""
+        n = int(x.numel() if hasattr(x, "numel") else x.size)
+        E = hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py))
+        cap = int(pairs.shape[0]) if pairs is not None else 0
+        cnt = _u64()
+        t = tuning or {}
+        opts = hrr_cull_opts(None, int(t.get("rangemin_variant", rangemin_variant)), shift_offset,
+                             int(t.get("blocks_per_sm", 0)), int(sample_index))
+        st = hrr_cull_host(self.handle, E, n, tree.handle, float(tau), C.byref(opts),
+                           _ptr(pairs) if cap else None, cap, C.byref(cnt))
         if st not in (HRR_OK, HRR_ERR_OVERFLOW):
             self.check(st)
         return st, int(cnt.value)

@@ -105,6 +105,15 @@ int hrr_destroy(hrr_ctx *ctx) {
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
     if (ctx->spill) cudaFree(ctx->spill);
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    if (ctx->host_eyes_dev) cudaFree(ctx->host_eyes_dev);
+    if (ctx->host_pairs_dev) cudaFree(ctx->host_pairs_dev);
+    for (int i = 0; i < HRR_HOST_SLICES; ++i) {
+        if (ctx->ev_in[i]) cudaEventDestroy(ctx->ev_in[i]);
+        if (ctx->ev_done[i]) cudaEventDestroy(ctx->ev_done[i]);
+    }
+    if (ctx->host_slices) cudaFreeHost(ctx->host_slices);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return HRR_OK;
@@ -274,6 +283,26 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
 int hrr_cull(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
              uint32_t *dev_pairs, uint64_t cap, uint64_t *out_count) {
     return hrr_cull_ex(ctx, eyes, n_eyes, tree, tau, nullptr, dev_pairs, cap, out_count);
+}
+
+int hrr_cull_host(hrr_ctx *ctx, hrr_eyes host_eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
+                  const hrr_cull_opts *opts, uint32_t *host_pairs, uint64_t cap, uint64_t *out_count) {
+    if (!ctx) return HRR_ERR_INVALID_ARG;
+    if (!out_count) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out_count is NULL");
+    *out_count = 0;
+    if (!tree) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tree is NULL");
+    if (tree->device != ctx->device) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tree lives on another device");
+    if (!(tau >= 0.0f) || !std::isfinite(tau)) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tau must be finite and >= 0");
+    if (n_eyes > 0 && (!host_eyes.x || !host_eyes.y || !host_eyes.z || !host_eyes.px || !host_eyes.py))
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "an eye array is NULL");
+    if (cap > 0 && !host_pairs) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "host_pairs is NULL");
+    if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
+    hrr_cull_opts o{};
+    if (opts) o = *opts;
+    if (o.rangemin_variant < 0 || o.rangemin_variant > 2 || o.blocks_per_sm > 64)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2 and blocks_per_sm <= 64");
+    DeviceGuard g(ctx->device);
+    return hrr_cull_host_impl(ctx, host_eyes, n_eyes, tree, tau, o, host_pairs, cap, out_count);
 }
 
 int hrr_last_cull_stats(const hrr_ctx *ctx, uint64_t *visits, uint64_t *accepted) {

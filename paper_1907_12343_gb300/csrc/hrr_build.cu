@@ -333,12 +333,13 @@ T *carve(char *&p, size_t count) {
 // ------------------------------------------------------------------------------------
 //
 // A top-down build, one level per pass: every range [f, l] of the level splits at the k
-// (children [f, k], [k+1, l]) that minimises
-//     C(k) = m_L (A_L + 1e-4) c_L + m_R (A_R + 1e-4) c_R
-// (c light count, m maximum intensity clamped at 0, A = dx dy + dy dz + dz dx of the box)
-// over every k in [f, l), in float with every operation rounded separately (no
-// contraction); a non-finite C never wins; ties go to the least |c_L - c_R|, then the
-// least k. Ranges deeper than the cost depth (root = 1)
+// (children [f, k], [k+1, l]) that minimises C(k) = w(L) + w(R) over every k in [f, l),
+//     w(X) = u^2 ((A + 0.1 P) + 1e-4) c sqrt(c),
+// with c the child's light count, u its maximum intensity (clamped at 0) times the
+// reciprocal of the range's, A = dx dy + dy dz + dz dx and P = dx + dy + dz of its box; in
+// float with every operation rounded separately (no contraction; sqrt and the reciprocal
+// correctly rounded). A non-finite C never wins; ties go to the least |c_L - c_R|, then
+// the least k. Ranges deeper than the cost depth (root = 1)
 // take the radix split, which bounds the height. Node numbering and parent links are those
 // of topology_kernel, so refit_kernel finishes the hierarchy unchanged.
 //
@@ -434,16 +435,23 @@ __device__ __forceinline__ Agg agg_unpack(float4 x, float4 y) {
 // Written by other blocks of the running kernel: read past L1.
 __device__ __forceinline__ Agg agg_load_cg(const AggRec *r) { return agg_unpack(__ldcg(&r->a), __ldcg(&r->b)); }
 
-__device__ __forceinline__ float half_area(const Agg &a) {
-    const float dx = __fsub_rn(a.hi[0], a.lo[0]), dy = __fsub_rn(a.hi[1], a.lo[1]), dz = __fsub_rn(a.hi[2], a.lo[2]);
-    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx));
+// w(X) of a child of c lights, given the reciprocal of the range's maximum intensity
+__device__ __forceinline__ float child_cost(const Agg &x, float inv, uint32_t c) {
+    const float u = __fmul_rn(fmaxf(x.m, 0.f), inv);
+    const float dx = __fsub_rn(x.hi[0], x.lo[0]), dy = __fsub_rn(x.hi[1], x.lo[1]), dz = __fsub_rn(x.hi[2], x.lo[2]);
+    const float a = __fadd_rn(__fadd_rn(__fmul_rn(dx, dy), __fmul_rn(dy, dz)), __fmul_rn(dz, dx));
+    const float p = __fadd_rn(__fadd_rn(dx, dy), dz);
+    const float g = __fadd_rn(__fadd_rn(a, __fmul_rn(0.1f, p)), 1e-4f);
+    const float cf = __uint2float_rn(c);
+    return __fmul_rn(__fmul_rn(__fmul_rn(u, u), g), __fmul_rn(cf, __fsqrt_rn(cf)));
 }
 
-// C(k) for children of cl and cr lights
+// C(k) for children of cl and cr lights; the reciprocal of a dark range's maximum is 0, and
+// a maximum below the smallest normal float counts as that float
 __device__ __forceinline__ float split_cost(const Agg &L, const Agg &R, uint32_t cl, uint32_t cr) {
-    const float ml = fmaxf(L.m, 0.f), mr = fmaxf(R.m, 0.f);
-    return __fadd_rn(__fmul_rn(__fmul_rn(ml, __fadd_rn(half_area(L), 1e-4f)), __uint2float_rn(cl)),
-                     __fmul_rn(__fmul_rn(mr, __fadd_rn(half_area(R), 1e-4f)), __uint2float_rn(cr)));
+    const float mx = fmaxf(fmaxf(L.m, 0.f), fmaxf(R.m, 0.f));
+    const float inv = mx > 0.f ? __fdiv_rn(1.f, fmaxf(mx, __int_as_float(0x00800000))) : 0.f;
+    return __fadd_rn(child_cost(L, inv, cl), child_cost(R, inv, cr));
 }
 
 __device__ __forceinline__ Best best_none() { return {__int_as_float(0x7f800000), kNoSplit, kNoSplit}; }

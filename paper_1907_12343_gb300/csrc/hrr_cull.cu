@@ -389,53 +389,50 @@ size_t hrr_cull_spill_entries(unsigned grid, uint32_t height) {
     return (size_t)grid * kWarps * hrr_cull_spill_cap(height);
 }
 
-int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tree *tree,
-                  float tau, const hrr_cull_opts &opts, uint32_t *pairs, uint64_t cap,
-                  uint64_t *out_count) {
-    if (((uintptr_t)pairs & 7u) != 0) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "dev_pairs must be 8-byte aligned");
-    cudaStream_t st = ctx->stream;
-    HRR_CUDA(ctx, cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), st));
-    if (n_eyes > 0) {
-        const hrr_tuning tn = hrr_tuning_of(opts);
-        const unsigned grid = hrr_cull_grid(ctx->sm_count, tn, false, n_eyes);
-        const size_t need = hrr_cull_spill_entries(grid, tree->height);
-        if (need > ctx->spill_entries) {  // the stack spill area grows with the grid and tree height
-            HRR_CUDA(ctx, cudaStreamSynchronize(st));
-            if (ctx->spill) cudaFree(ctx->spill);
-            ctx->spill = nullptr;
-            ctx->spill_entries = 0;
-            if (cudaMalloc(&ctx->spill, need * sizeof(uint2)) != cudaSuccess) {
-                cudaGetLastError();
-                return hrr_fail(ctx, HRR_ERR_OOM, "traversal stack spill area");
-            }
-            ctx->spill_entries = need;
-        }
-        Frame fr{};
-        fr.ex = E.x; fr.ey = E.y; fr.ez = E.z; fr.px = E.px; fr.py = E.py;
-        fr.nodes = reinterpret_cast<const float4 *>(tree->nodes);
-        fr.perm = tree->perm;
-        fr.tile = hrr_tile_layer(ctx->tile, ctx->tile_w, ctx->tile_h, ctx->tile_d, opts.sample_index);
-        fr.pairs = reinterpret_cast<uint2 *>(pairs);
-        fr.cap = cap;
-        fr.counts = ctx->counters;  // [0] accepted, [1] visits
-        fr.eye_visits = opts.eye_visits;
-        fr.n_lights = tree->n;
-        fr.tile_w = ctx->tile_w; fr.tile_h = ctx->tile_h;
-        fr.shift_offset = opts.shift_offset;
-        fr.tau = tau;
-        fr.eye_begin = 0;
-        fr.cursor_begin = 0;
-        const Launch Lc{1, hrr_cull_spill_cap(tree->height), n_eyes, ctx->counters + 3, ctx->counters + 2,
-                        reinterpret_cast<uint2 *>(ctx->spill)};
-        hrr_timing_begin(ctx);
-        const cudaError_t e = launch_single(tn, grid, Lc, fr, st);
-        hrr_timing_end(ctx);
-        ++ctx->launches;
-        HRR_CUDA(ctx, e);
+namespace {
+
+// Grows the context's stack spill area to hold `need` entries (synchronises the stream first).
+int ensure_spill(hrr_ctx *ctx, size_t need) {
+    if (need <= ctx->spill_entries) return HRR_OK;
+    HRR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->spill) cudaFree(ctx->spill);
+    ctx->spill = nullptr;
+    ctx->spill_entries = 0;
+    if (cudaMalloc(&ctx->spill, need * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        return hrr_fail(ctx, HRR_ERR_OOM, "traversal stack spill area");
     }
+    ctx->spill_entries = need;
+    return HRR_OK;
+}
+
+// The single-frame descriptor of one culling launch over eyes [eye_begin, eye_begin + n).
+Frame single_frame(const hrr_ctx *ctx, const hrr_eyes &E, const hrr_tree *tree, float tau, const hrr_cull_opts &opts,
+                   uint32_t *pairs, uint64_t cap, uint32_t eye_begin) {
+    Frame fr{};
+    fr.ex = E.x; fr.ey = E.y; fr.ez = E.z; fr.px = E.px; fr.py = E.py;
+    fr.nodes = reinterpret_cast<const float4 *>(tree->nodes);
+    fr.perm = tree->perm;
+    fr.tile = hrr_tile_layer(ctx->tile, ctx->tile_w, ctx->tile_h, ctx->tile_d, opts.sample_index);
+    fr.pairs = reinterpret_cast<uint2 *>(pairs);
+    fr.cap = cap;
+    fr.counts = ctx->counters;  // [0] accepted, [1] visits
+    fr.eye_visits = opts.eye_visits;
+    fr.n_lights = tree->n;
+    fr.tile_w = ctx->tile_w; fr.tile_h = ctx->tile_h;
+    fr.shift_offset = opts.shift_offset;
+    fr.tau = tau;
+    fr.eye_begin = eye_begin;
+    fr.cursor_begin = 0;
+    return fr;
+}
+
+// Reads the context's counters after a cull (synchronising the stream) and turns them into
+// the call's status.
+int finish_cull(hrr_ctx *ctx, uint64_t cap, uint64_t *out_count) {
     HRR_CUDA(ctx, cudaMemcpyAsync(ctx->host_counters, ctx->counters, 3 * sizeof(unsigned long long),
-                                  cudaMemcpyDeviceToHost, st));
-    HRR_CUDA(ctx, cudaStreamSynchronize(st));
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    HRR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     const uint64_t count = ctx->host_counters[0];
     ctx->last_accepted = count;
     ctx->last_visits = ctx->host_counters[1];
@@ -446,6 +443,138 @@ int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tr
         return hrr_fail(ctx, HRR_ERR_DEVICE, "corrupt node record");
     if (count > cap) return hrr_fail(ctx, HRR_ERR_OVERFLOW, "output capacity too small");
     return HRR_OK;
+}
+
+}  // namespace
+
+int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tree *tree,
+                  float tau, const hrr_cull_opts &opts, uint32_t *pairs, uint64_t cap,
+                  uint64_t *out_count) {
+    if (((uintptr_t)pairs & 7u) != 0) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "dev_pairs must be 8-byte aligned");
+    cudaStream_t st = ctx->stream;
+    HRR_CUDA(ctx, cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), st));
+    if (n_eyes > 0) {
+        const hrr_tuning tn = hrr_tuning_of(opts);
+        const unsigned grid = hrr_cull_grid(ctx->sm_count, tn, false, n_eyes);
+        if (int rc = ensure_spill(ctx, hrr_cull_spill_entries(grid, tree->height))) return rc;
+        const Frame fr = single_frame(ctx, E, tree, tau, opts, pairs, cap, 0);
+        const Launch Lc{1, hrr_cull_spill_cap(tree->height), n_eyes, ctx->counters + 3, ctx->counters + 2,
+                        reinterpret_cast<uint2 *>(ctx->spill)};
+        hrr_timing_begin(ctx);
+        const cudaError_t e = launch_single(tn, grid, Lc, fr, st);
+        hrr_timing_end(ctx);
+        ++ctx->launches;
+        HRR_CUDA(ctx, e);
+    }
+    return finish_cull(ctx, cap, out_count);
+}
+
+// Eyes from host memory, pairs to host memory. The eyes are culled in up to
+// HRR_HOST_SLICES slices, one launch each, in order on the context stream; the copy stream
+// uploads each slice's eyes ahead of its launch and downloads the pairs a slice appended
+// while the next slice runs (the host waits for each slice's pair count). Launches append
+// to one buffer through one counter, in stream order, so slice i's pairs are the entries
+// between the counts after launches i - 1 and i.
+int hrr_cull_host_impl(hrr_ctx *ctx, const hrr_eyes &H, uint32_t n_eyes, const hrr_tree *tree, float tau,
+                       const hrr_cull_opts &opts, uint32_t *host_pairs, uint64_t cap, uint64_t *out_count) {
+    cudaStream_t st = ctx->stream;
+    if (!ctx->copy_stream) {
+        HRR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        for (int i = 0; i < HRR_HOST_SLICES; ++i) {
+            HRR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming));
+            HRR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming));
+        }
+        if (cudaMallocHost(&ctx->host_slices, HRR_HOST_SLICES * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->host_slices = nullptr;
+            return hrr_fail(ctx, HRR_ERR_OOM, "pinned slice counts");
+        }
+    }
+    if (!ctx->host_slices) return hrr_fail(ctx, HRR_ERR_OOM, "pinned slice counts");
+    // device copies: x, y, z (4 B each) and px, py (2 B each) per eye; 8 B per pair
+    auto grow = [&](void *&buf, size_t &have, size_t want, size_t unit, const char *what) -> int {
+        if (want <= have) return HRR_OK;
+        HRR_CUDA(ctx, cudaStreamSynchronize(st));
+        if (buf) cudaFree(buf);
+        buf = nullptr;
+        have = 0;
+        if (cudaMalloc(&buf, want * unit + 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return hrr_fail(ctx, HRR_ERR_OOM, what);
+        }
+        have = want;
+        return HRR_OK;
+    };
+    if (int rc = grow(ctx->host_eyes_dev, ctx->host_eyes_cap, n_eyes, 16, "device copy of the eyes")) return rc;
+    if (int rc = grow(ctx->host_pairs_dev, ctx->host_pairs_cap, cap, 8, "device pair buffer")) return rc;
+    char *eb = static_cast<char *>(ctx->host_eyes_dev);
+    const size_t ne = ctx->host_eyes_cap;
+    auto at = [&](size_t off) { return eb + ((off + 255) & ~size_t(255)); };
+    float *dx = reinterpret_cast<float *>(at(0));
+    float *dy = reinterpret_cast<float *>(at((size_t)(reinterpret_cast<char *>(dx + ne) - eb)));
+    float *dz = reinterpret_cast<float *>(at((size_t)(reinterpret_cast<char *>(dy + ne) - eb)));
+    uint16_t *dpx = reinterpret_cast<uint16_t *>(at((size_t)(reinterpret_cast<char *>(dz + ne) - eb)));
+    uint16_t *dpy = reinterpret_cast<uint16_t *>(at((size_t)(reinterpret_cast<char *>(dpx + ne) - eb)));
+    uint32_t *dpairs = static_cast<uint32_t *>(ctx->host_pairs_dev);
+    const hrr_eyes D{dx, dy, dz, dpx, dpy};
+
+    HRR_CUDA(ctx, cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), st));
+    // slices of about 2^19 eyes or more
+    const uint32_t slices = n_eyes == 0 ? 0u : std::max(1u, std::min<uint32_t>(HRR_HOST_SLICES, (n_eyes + (1u << 18)) >> 19));
+    const hrr_tuning tn = hrr_tuning_of(opts);
+    if (slices) {
+        const unsigned grid = hrr_cull_grid(ctx->sm_count, tn, false, (n_eyes + slices - 1) / slices);
+        if (int rc = ensure_spill(ctx, hrr_cull_spill_entries(grid, tree->height))) return rc;
+    }
+    // The copy stream must not overwrite the device eyes or pairs while earlier work reads them.
+    HRR_CUDA(ctx, cudaEventRecord(ctx->ev_done[0], st));
+    HRR_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[0], 0));
+    cudaError_t e = cudaSuccess;
+    uint32_t enqueued = 0;
+    for (uint32_t i = 0; i < slices && e == cudaSuccess; ++i) {
+        const uint32_t e0 = (uint32_t)((uint64_t)n_eyes * i / slices), e1 = (uint32_t)((uint64_t)n_eyes * (i + 1) / slices);
+        const size_t m = e1 - e0;
+        cudaStream_t cs = ctx->copy_stream;
+        e = cudaMemcpyAsync(dx + e0, H.x + e0, m * 4, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dy + e0, H.y + e0, m * 4, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dz + e0, H.z + e0, m * 4, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpx + e0, H.px + e0, m * 2, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpy + e0, H.py + e0, m * 2, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in[i], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_in[i], 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters + 3, 0, sizeof(unsigned long long), st);  // cursor
+        if (e == cudaSuccess) {
+            const unsigned grid = hrr_cull_grid(ctx->sm_count, tn, false, m);
+            const Frame fr = single_frame(ctx, D, tree, tau, opts, dpairs, cap, e0);
+            const Launch Lc{1, hrr_cull_spill_cap(tree->height), m, ctx->counters + 3, ctx->counters + 2,
+                            reinterpret_cast<uint2 *>(ctx->spill)};
+            e = launch_single(tn, grid, Lc, fr, st);
+            ++ctx->launches;
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&ctx->host_slices[i], ctx->counters, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_done[i], st);
+        if (e == cudaSuccess) enqueued = i + 1;
+    }
+    uint64_t done = 0;  // pairs already on their way to the host
+    for (uint32_t i = 0; i < enqueued && e == cudaSuccess; ++i) {
+        e = cudaEventSynchronize(ctx->ev_done[i]);
+        const uint64_t c = std::min<uint64_t>(ctx->host_slices[i], cap);
+        if (e == cudaSuccess && c > done) {
+            e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[i], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(host_pairs + 2 * done, dpairs + 2 * done, (c - done) * 8, cudaMemcpyDeviceToHost,
+                                    ctx->copy_stream);
+            done = c;
+        }
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(ctx->copy_stream);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        return hrr_cuda_fail(ctx, e, "culling with host buffers");
+    }
+    return finish_cull(ctx, cap, out_count);
 }
 
 cudaError_t hrr_cull_batch_enqueue(unsigned grid, const hrr_cull_frame_t *frames, uint32_t n_frames,

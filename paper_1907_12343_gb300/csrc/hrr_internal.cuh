@@ -13,6 +13,9 @@
 // Host-side objects
 // ------------------------------------------------------------------------------------
 
+// Most slices hrr_cull_host splits the eyes into.
+#define HRR_HOST_SLICES 4
+
 struct hrr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -34,6 +37,15 @@ struct hrr_ctx {
     // traversal stack spill area (grown on demand by hrr_cull)
     void *spill = nullptr;
     size_t spill_entries = 0;
+    // hrr_cull_host: device copies of the eyes and the pairs (grown on demand), a copy
+    // stream, per-slice events and pinned per-slice pair counts (created on first use)
+    void *host_eyes_dev = nullptr;
+    size_t host_eyes_cap = 0;  // eyes
+    void *host_pairs_dev = nullptr;
+    size_t host_pairs_cap = 0;  // pairs
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_in[HRR_HOST_SLICES] = {}, ev_done[HRR_HOST_SLICES] = {};
+    unsigned long long *host_slices = nullptr;
     std::string err;
 };
 
@@ -142,6 +154,9 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &lights, uint32_t n, hrr_tree 
 int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &eyes, uint32_t n_eyes, const hrr_tree *tree,
                   float tau, const hrr_cull_opts &opts, uint32_t *pairs, uint64_t cap,
                   uint64_t *out_count);
+int hrr_cull_host_impl(hrr_ctx *ctx, const hrr_eyes &host_eyes, uint32_t n_eyes, const hrr_tree *tree,
+                       float tau, const hrr_cull_opts &opts, uint32_t *host_pairs, uint64_t cap,
+                       uint64_t *out_count);
 int hrr_range_min_impl(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r,
                        uint32_t *out_min, uint32_t *out_argmin, uint64_t n, int variant);
 

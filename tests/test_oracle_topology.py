@@ -53,20 +53,28 @@ def test_two_clusters_are_separated_at_the_root():
 
 def _rule(pos, inten, f, l):
     """The split rule restated in float32 numpy (every operation rounded to float32): every
-    split, cost, ties."""
+    split, the child cost u^2 ((A + 0.1 P) + 1e-4) c sqrt(c) with u the child's maximum over
+    the range's, ties."""
     f32 = np.float32
     P = pos[f:l + 1].astype(f32)
     I = inten[f:l + 1].astype(f32)
-    eps = f32(1e-4)
+
+    def child(m, inv, d, c):
+        u = m * inv
+        a = (d[0] * d[1] + d[1] * d[2]) + d[2] * d[0]
+        per = (d[0] + d[1]) + d[2]
+        g = (a + f32(0.1) * per) + f32(1e-4)
+        c = f32(c)
+        return ((u * u) * g) * (c * np.sqrt(c))
+
     best = None
     for k in range(f, l):
         L, R = P[: k - f + 1], P[k - f + 1:]
-        dl, dr = L.max(0) - L.min(0), R.max(0) - R.min(0)
-        al = (dl[0] * dl[1] + dl[1] * dl[2]) + dl[2] * dl[0]
-        ar = (dr[0] * dr[1] + dr[1] * dr[2]) + dr[2] * dr[0]
         ml, mr = max(I[: k - f + 1].max(), f32(0)), max(I[k - f + 1:].max(), f32(0))
+        mx = max(ml, mr)
+        inv = f32(1) / max(mx, f32(np.finfo(f32).tiny)) if mx > 0 else f32(0)
         cl, cr = k - f + 1, l - k
-        cost = (ml * (al + eps)) * f32(cl) + (mr * (ar + eps)) * f32(cr)
+        cost = child(ml, inv, L.max(0) - L.min(0), cl) + child(mr, inv, R.max(0) - R.min(0), cr)
         assert cost.dtype == f32
         key = (float(cost), abs(cl - cr), k)
         best = key if best is None or key < best else best
