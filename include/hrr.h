@@ -252,9 +252,11 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
  * n_eyes entries each) and the accepted pairs written to host memory (host_pairs: 2 * cap
  * uint32), as (eye index, original light id) with the same set as hrr_cull_ex gives for the
  * same eyes and options. Pinned host memory lets the copies overlap the culling: the eyes
- * are culled in up to four slices in order, each slice's eyes are copied in ahead of it and
- * its pairs copied out while the next slice runs. The context keeps device copies of the
- * eyes and pairs (grown on demand, freed by hrr_destroy) and a copy stream. Statuses as in
+ * are culled in up to eight slices of at least about 2^18 eyes, launched alternately on the
+ * context stream and a second stream so that consecutive slices overlap; each slice's eyes
+ * are copied in ahead of it and its pairs copied out while the next slice runs. The
+ * context keeps device copies of the eyes and two pair buffers of cap pairs (grown on
+ * demand, freed by hrr_destroy), a second stream and a copy stream. Statuses as in
  * hrr_cull_ex (HRR_ERR_OVERFLOW: *out_count holds the need, the first cap pairs of the
  * buffer are written). opts may be NULL; its eye_visits, if set, is device memory.
  * Synchronous. */

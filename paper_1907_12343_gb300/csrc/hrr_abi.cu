@@ -106,14 +106,19 @@ int hrr_destroy(hrr_ctx *ctx) {
     if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
     if (ctx->spill) cudaFree(ctx->spill);
     if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
     if (ctx->host_eyes_dev) cudaFree(ctx->host_eyes_dev);
     if (ctx->host_pairs_dev) cudaFree(ctx->host_pairs_dev);
+    if (ctx->slice_counters) cudaFree(ctx->slice_counters);
+    if (ctx->ev_first) cudaEventDestroy(ctx->ev_first);
     for (int i = 0; i < HRR_HOST_SLICES; ++i) {
         if (ctx->ev_in[i]) cudaEventDestroy(ctx->ev_in[i]);
         if (ctx->ev_done[i]) cudaEventDestroy(ctx->ev_done[i]);
+        if (ctx->ev_out[i]) cudaEventDestroy(ctx->ev_out[i]);
     }
     if (ctx->host_slices) cudaFreeHost(ctx->host_slices);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return HRR_OK;

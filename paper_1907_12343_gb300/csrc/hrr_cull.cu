@@ -27,6 +27,8 @@
 // frames, each warp finds its eye's frame by binary search over the frames' cursor offsets,
 // and the frames' descriptors are staged in shared memory. Frames of different sizes share
 // the launch without any per-frame tail.
+#include <algorithm>
+
 #include "hrr_internal.cuh"
 
 namespace {
@@ -470,28 +472,32 @@ int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tr
 }
 
 // Eyes from host memory, pairs to host memory. The eyes are culled in up to
-// HRR_HOST_SLICES slices, one launch each, in order on the context stream; the copy stream
-// uploads each slice's eyes ahead of its launch and downloads the pairs a slice appended
-// while the next slice runs (the host waits for each slice's pair count). Launches append
-// to one buffer through one counter, in stream order, so slice i's pairs are the entries
-// between the counts after launches i - 1 and i.
+// HRR_HOST_SLICES slices, one launch each, alternating between two streams so that a
+// slice's blocks fill the SMs its predecessor's last eyes leave idle. Each slice counts
+// into its own counters and appends to one of two device pair buffers (slice i to buffer
+// i mod 2); the copy stream uploads every slice's eyes first and then downloads each
+// slice's pairs, in slice order, once the host has read that slice's count. Slice i + 2
+// is enqueued after slice i's download, on which it waits before reusing the buffer.
 int hrr_cull_host_impl(hrr_ctx *ctx, const hrr_eyes &H, uint32_t n_eyes, const hrr_tree *tree, float tau,
                        const hrr_cull_opts &opts, uint32_t *host_pairs, uint64_t cap, uint64_t *out_count) {
     cudaStream_t st = ctx->stream;
     if (!ctx->copy_stream) {
         HRR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        HRR_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->stream2, cudaStreamNonBlocking));
+        HRR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_first, cudaEventDisableTiming));
         for (int i = 0; i < HRR_HOST_SLICES; ++i) {
             HRR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming));
             HRR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming));
+            HRR_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_out[i], cudaEventDisableTiming));
         }
-        if (cudaMallocHost(&ctx->host_slices, HRR_HOST_SLICES * sizeof(unsigned long long)) != cudaSuccess) {
+        if (cudaMalloc(&ctx->slice_counters, HRR_HOST_SLICES * 4 * sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMallocHost(&ctx->host_slices, HRR_HOST_SLICES * 4 * sizeof(unsigned long long)) != cudaSuccess) {
             cudaGetLastError();
-            ctx->host_slices = nullptr;
-            return hrr_fail(ctx, HRR_ERR_OOM, "pinned slice counts");
+            return hrr_fail(ctx, HRR_ERR_OOM, "slice counters");
         }
     }
-    if (!ctx->host_slices) return hrr_fail(ctx, HRR_ERR_OOM, "pinned slice counts");
-    // device copies: x, y, z (4 B each) and px, py (2 B each) per eye; 8 B per pair
+    if (!ctx->host_slices || !ctx->slice_counters) return hrr_fail(ctx, HRR_ERR_OOM, "slice counters");
+    // device copies: x, y, z (4 B each) and px, py (2 B each) per eye; two buffers of 8 B pairs
     auto grow = [&](void *&buf, size_t &have, size_t want, size_t unit, const char *what) -> int {
         if (want <= have) return HRR_OK;
         HRR_CUDA(ctx, cudaStreamSynchronize(st));
@@ -506,75 +512,107 @@ int hrr_cull_host_impl(hrr_ctx *ctx, const hrr_eyes &H, uint32_t n_eyes, const h
         return HRR_OK;
     };
     if (int rc = grow(ctx->host_eyes_dev, ctx->host_eyes_cap, n_eyes, 16, "device copy of the eyes")) return rc;
-    if (int rc = grow(ctx->host_pairs_dev, ctx->host_pairs_cap, cap, 8, "device pair buffer")) return rc;
+    if (int rc = grow(ctx->host_pairs_dev, ctx->host_pairs_cap, cap, 16, "device pair buffers")) return rc;
     char *eb = static_cast<char *>(ctx->host_eyes_dev);
     const size_t ne = ctx->host_eyes_cap;
-    auto at = [&](size_t off) { return eb + ((off + 255) & ~size_t(255)); };
-    float *dx = reinterpret_cast<float *>(at(0));
-    float *dy = reinterpret_cast<float *>(at((size_t)(reinterpret_cast<char *>(dx + ne) - eb)));
-    float *dz = reinterpret_cast<float *>(at((size_t)(reinterpret_cast<char *>(dy + ne) - eb)));
-    uint16_t *dpx = reinterpret_cast<uint16_t *>(at((size_t)(reinterpret_cast<char *>(dz + ne) - eb)));
-    uint16_t *dpy = reinterpret_cast<uint16_t *>(at((size_t)(reinterpret_cast<char *>(dpx + ne) - eb)));
-    uint32_t *dpairs = static_cast<uint32_t *>(ctx->host_pairs_dev);
+    auto at = [&](const void *end) {
+        const size_t off = (size_t)(static_cast<const char *>(end) - eb);
+        return eb + ((off + 255) & ~size_t(255));
+    };
+    float *dx = reinterpret_cast<float *>(eb);
+    float *dy = reinterpret_cast<float *>(at(dx + ne));
+    float *dz = reinterpret_cast<float *>(at(dy + ne));
+    uint16_t *dpx = reinterpret_cast<uint16_t *>(at(dz + ne));
+    uint16_t *dpy = reinterpret_cast<uint16_t *>(at(dpx + ne));
+    uint32_t *buf[2] = {static_cast<uint32_t *>(ctx->host_pairs_dev),
+                        static_cast<uint32_t *>(ctx->host_pairs_dev) + 2 * ctx->host_pairs_cap};
     const hrr_eyes D{dx, dy, dz, dpx, dpy};
 
-    HRR_CUDA(ctx, cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), st));
-    // slices of about 2^19 eyes or more
-    const uint32_t slices = n_eyes == 0 ? 0u : std::max(1u, std::min<uint32_t>(HRR_HOST_SLICES, (n_eyes + (1u << 18)) >> 19));
+    // slices of about 2^18 eyes or more
+    const uint32_t slices = n_eyes == 0 ? 0u : std::max(1u, std::min<uint32_t>(HRR_HOST_SLICES, (n_eyes + (1u << 17)) >> 18));
     const hrr_tuning tn = hrr_tuning_of(opts);
     if (slices) {
         const unsigned grid = hrr_cull_grid(ctx->sm_count, tn, false, (n_eyes + slices - 1) / slices);
-        if (int rc = ensure_spill(ctx, hrr_cull_spill_entries(grid, tree->height))) return rc;
+        // two slices may run at once, each with its own spill area
+        if (int rc = ensure_spill(ctx, 2 * hrr_cull_spill_entries(grid, tree->height))) return rc;
     }
-    // The copy stream must not overwrite the device eyes or pairs while earlier work reads them.
-    HRR_CUDA(ctx, cudaEventRecord(ctx->ev_done[0], st));
-    HRR_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[0], 0));
+    cudaStream_t cs[2] = {st, ctx->stream2};
+    HRR_CUDA(ctx, cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), st));
+    HRR_CUDA(ctx, cudaMemsetAsync(ctx->slice_counters, 0, HRR_HOST_SLICES * 4 * sizeof(unsigned long long), st));
+    HRR_CUDA(ctx, cudaEventRecord(ctx->ev_first, st));
+    HRR_CUDA(ctx, cudaStreamWaitEvent(ctx->stream2, ctx->ev_first, 0));
+    HRR_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_first, 0));
+    auto bounds = [&](uint32_t i, uint32_t &e0, uint32_t &e1) {
+        e0 = (uint32_t)((uint64_t)n_eyes * i / slices);
+        e1 = (uint32_t)((uint64_t)n_eyes * (i + 1) / slices);
+    };
     cudaError_t e = cudaSuccess;
-    uint32_t enqueued = 0;
-    for (uint32_t i = 0; i < slices && e == cudaSuccess; ++i) {
-        const uint32_t e0 = (uint32_t)((uint64_t)n_eyes * i / slices), e1 = (uint32_t)((uint64_t)n_eyes * (i + 1) / slices);
+    for (uint32_t i = 0; i < slices && e == cudaSuccess; ++i) {  // every slice's eyes, in order
+        uint32_t e0, e1;
+        bounds(i, e0, e1);
         const size_t m = e1 - e0;
-        cudaStream_t cs = ctx->copy_stream;
-        e = cudaMemcpyAsync(dx + e0, H.x + e0, m * 4, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dy + e0, H.y + e0, m * 4, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dz + e0, H.z + e0, m * 4, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dpx + e0, H.px + e0, m * 2, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(dpy + e0, H.py + e0, m * 2, cudaMemcpyHostToDevice, cs);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in[i], cs);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->ev_in[i], 0);
-        if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters + 3, 0, sizeof(unsigned long long), st);  // cursor
-        if (e == cudaSuccess) {
-            const unsigned grid = hrr_cull_grid(ctx->sm_count, tn, false, m);
-            const Frame fr = single_frame(ctx, D, tree, tau, opts, dpairs, cap, e0);
-            const Launch Lc{1, hrr_cull_spill_cap(tree->height), m, ctx->counters + 3, ctx->counters + 2,
-                            reinterpret_cast<uint2 *>(ctx->spill)};
-            e = launch_single(tn, grid, Lc, fr, st);
-            ++ctx->launches;
-        }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&ctx->host_slices[i], ctx->counters, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_done[i], st);
-        if (e == cudaSuccess) enqueued = i + 1;
+        cudaStream_t c = ctx->copy_stream;
+        e = cudaMemcpyAsync(dx + e0, H.x + e0, m * 4, cudaMemcpyHostToDevice, c);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dy + e0, H.y + e0, m * 4, cudaMemcpyHostToDevice, c);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dz + e0, H.z + e0, m * 4, cudaMemcpyHostToDevice, c);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpx + e0, H.px + e0, m * 2, cudaMemcpyHostToDevice, c);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dpy + e0, H.py + e0, m * 2, cudaMemcpyHostToDevice, c);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_in[i], c);
     }
-    uint64_t done = 0;  // pairs already on their way to the host
+    const unsigned grid_cap = hrr_cull_grid(ctx->sm_count, tn, false, (n_eyes + slices - 1) / std::max(1u, slices));
+    auto enqueue = [&](uint32_t i) -> cudaError_t {
+        uint32_t e0, e1;
+        bounds(i, e0, e1);
+        cudaStream_t s = cs[i & 1];
+        unsigned long long *cnt = ctx->slice_counters + 4 * i;  // [0] accepted, [1] visits, [3] cursor
+        cudaError_t r = cudaStreamWaitEvent(s, ctx->ev_in[i], 0);
+        if (r == cudaSuccess && i >= 2) r = cudaStreamWaitEvent(s, ctx->ev_out[i - 2], 0);  // buffer reuse
+        if (r != cudaSuccess) return r;
+        Frame fr = single_frame(ctx, D, tree, tau, opts, buf[i & 1], cap, e0);
+        fr.counts = cnt;
+        const Launch Lc{1, hrr_cull_spill_cap(tree->height), (unsigned long long)(e1 - e0), cnt + 3, ctx->counters + 2,
+                        reinterpret_cast<uint2 *>(ctx->spill) + (i & 1) * hrr_cull_spill_entries(grid_cap, tree->height)};
+        r = launch_single(tn, hrr_cull_grid(ctx->sm_count, tn, false, e1 - e0), Lc, fr, s);
+        ++ctx->launches;
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(&ctx->host_slices[4 * i], cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        if (r == cudaSuccess) r = cudaEventRecord(ctx->ev_done[i], s);
+        return r;
+    };
+    uint32_t enqueued = 0;
+    for (uint32_t i = 0; i < std::min(slices, 2u) && e == cudaSuccess; ++i)
+        if ((e = enqueue(i)) == cudaSuccess) enqueued = i + 1;
+    uint64_t need = 0, placed = 0, visits = 0;
     for (uint32_t i = 0; i < enqueued && e == cudaSuccess; ++i) {
         e = cudaEventSynchronize(ctx->ev_done[i]);
-        const uint64_t c = std::min<uint64_t>(ctx->host_slices[i], cap);
-        if (e == cudaSuccess && c > done) {
-            e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[i], 0);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(host_pairs + 2 * done, dpairs + 2 * done, (c - done) * 8, cudaMemcpyDeviceToHost,
-                                    ctx->copy_stream);
-            done = c;
+        if (e != cudaSuccess) break;
+        const uint64_t c = ctx->host_slices[4 * i];
+        visits += ctx->host_slices[4 * i + 1];
+        const uint64_t fit = std::min<uint64_t>({c, cap, cap - placed});
+        e = cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_done[i], 0);
+        if (e == cudaSuccess && fit)
+            e = cudaMemcpyAsync(host_pairs + 2 * placed, buf[i & 1], fit * 8, cudaMemcpyDeviceToHost, ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_out[i], ctx->copy_stream);
+        need += c;
+        placed += fit;
+        if (e == cudaSuccess && i + 2 < slices) {
+            if ((e = enqueue(i + 2)) == cudaSuccess) enqueued = i + 3;
         }
     }
-    const cudaError_t e2 = cudaStreamSynchronize(ctx->copy_stream);
-    if (e == cudaSuccess) e = e2;
-    if (e != cudaSuccess) {
-        cudaStreamSynchronize(st);
-        return hrr_cuda_fail(ctx, e, "culling with host buffers");
+    for (cudaStream_t s : {ctx->copy_stream, ctx->stream2, st}) {
+        const cudaError_t e2 = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = e2;
     }
-    return finish_cull(ctx, cap, out_count);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->host_counters, ctx->counters, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return hrr_cuda_fail(ctx, e, "culling with host buffers");
+    ctx->last_accepted = need;
+    ctx->last_visits = visits;
+    *out_count = need;
+    if (ctx->host_counters[2] & HRR_FLAG_STACK) return hrr_fail(ctx, HRR_ERR_DEVICE, "traversal stack overflow");
+    if (ctx->host_counters[2] & HRR_FLAG_TOPOLOGY) return hrr_fail(ctx, HRR_ERR_DEVICE, "corrupt node record");
+    if (need > cap) return hrr_fail(ctx, HRR_ERR_OVERFLOW, "output capacity too small");
+    return HRR_OK;
 }
 
 cudaError_t hrr_cull_batch_enqueue(unsigned grid, const hrr_cull_frame_t *frames, uint32_t n_frames,

@@ -14,7 +14,7 @@
 // ------------------------------------------------------------------------------------
 
 // Most slices hrr_cull_host splits the eyes into.
-#define HRR_HOST_SLICES 4
+#define HRR_HOST_SLICES 8
 
 struct hrr_ctx {
     int device = 0;
@@ -37,15 +37,18 @@ struct hrr_ctx {
     // traversal stack spill area (grown on demand by hrr_cull)
     void *spill = nullptr;
     size_t spill_entries = 0;
-    // hrr_cull_host: device copies of the eyes and the pairs (grown on demand), a copy
-    // stream, per-slice events and pinned per-slice pair counts (created on first use)
+    // hrr_cull_host: device copies of the eyes and two pair buffers (grown on demand), a
+    // second compute stream and a copy stream, per-slice events and counters (device and
+    // pinned), all created on first use
     void *host_eyes_dev = nullptr;
     size_t host_eyes_cap = 0;  // eyes
     void *host_pairs_dev = nullptr;
-    size_t host_pairs_cap = 0;  // pairs
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_in[HRR_HOST_SLICES] = {}, ev_done[HRR_HOST_SLICES] = {};
-    unsigned long long *host_slices = nullptr;
+    size_t host_pairs_cap = 0;  // pairs per buffer
+    cudaStream_t stream2 = nullptr, copy_stream = nullptr;
+    cudaEvent_t ev_first = nullptr;
+    cudaEvent_t ev_in[HRR_HOST_SLICES] = {}, ev_done[HRR_HOST_SLICES] = {}, ev_out[HRR_HOST_SLICES] = {};
+    unsigned long long *slice_counters = nullptr;  // device, 4 per slice
+    unsigned long long *host_slices = nullptr;     // pinned, 4 per slice
     std::string err;
 };
 
