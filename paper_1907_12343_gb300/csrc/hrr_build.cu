@@ -446,11 +446,16 @@ __device__ __forceinline__ float child_cost(const Agg &x, float inv, uint32_t c)
     return __fmul_rn(__fmul_rn(__fmul_rn(u, u), g), __fmul_rn(cf, __fsqrt_rn(cf)));
 }
 
-// C(k) for children of cl and cr lights; the reciprocal of a dark range's maximum is 0, and
-// a maximum below the smallest normal float counts as that float
-__device__ __forceinline__ float split_cost(const Agg &L, const Agg &R, uint32_t cl, uint32_t cr) {
-    const float mx = fmaxf(fmaxf(L.m, 0.f), fmaxf(R.m, 0.f));
-    const float inv = mx > 0.f ? __fdiv_rn(1.f, fmaxf(mx, __int_as_float(0x00800000))) : 0.f;
+// Reciprocal of a range's maximum intensity m: 0 for a dark range, and a maximum below the
+// smallest normal float counts as that float.
+__device__ __forceinline__ float range_inv(float m) {
+    const float mx = fmaxf(m, 0.f);
+    return mx > 0.f ? __fdiv_rn(1.f, fmaxf(mx, __int_as_float(0x00800000))) : 0.f;
+}
+
+// C(k) for children of cl and cr lights, given range_inv of the range's maximum (the larger
+// of the children's)
+__device__ __forceinline__ float split_cost(const Agg &L, const Agg &R, uint32_t cl, uint32_t cr, float inv) {
     return __fadd_rn(child_cost(L, inv, cl), child_cost(R, inv, cr));
 }
 
@@ -539,6 +544,7 @@ __device__ __forceinline__ void run_best(const float4 (&p)[R], uint32_t cnt, uin
     suf[R] = after;
 #pragma unroll
     for (int i = R - 1; i >= 0; --i) suf[i] = (uint32_t)i < cnt ? agg_join(agg_of(p[i]), suf[i + 1]) : suf[i + 1];
+    const float inv = range_inv(fmaxf(before.m, suf[0].m));  // the same for every split of the range
     Agg pre = before;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -547,7 +553,7 @@ __device__ __forceinline__ void run_best(const float4 (&p)[R], uint32_t cnt, uin
             const uint32_t k = a + i;
             if (k < l) {
                 const uint32_t cl = k - f + 1, cr = l - k;
-                best_take(b, {split_cost(pre, suf[i + 1], cl, cr), cl > cr ? cl - cr : cr - cl, k});
+                best_take(b, {split_cost(pre, suf[i + 1], cl, cr, inv), cl > cr ? cl - cr : cr - cl, k});
             }
         }
     }
@@ -643,7 +649,7 @@ __global__ void __launch_bounds__(kSplitThreads) subtree_warp_kernel(const Seg *
         Best b = best_none();
         if (lane < ll) {
             const uint32_t cl = i - g.f + 1, cr = g.l - i;
-            b = {split_cost(pre, right, cl, cr), cl > cr ? cl - cr : cr - cl, i};
+            b = {split_cost(pre, right, cl, cr, range_inv(fmaxf(pre.m, right.m))), cl > cr ? cl - cr : cr - cl, i};
         }
         for (int d = 1; d < 32; d <<= 1) {  // the range's best split, in its first lane
             const Best ob = {__shfl_down_sync(0xFFFFFFFFu, b.c, d), __shfl_down_sync(0xFFFFFFFFu, b.d, d),
