@@ -237,12 +237,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32", "data": "synthetic",
-            "config": {"workload": f"frame {args.eyes} eyes x {n_l} Gaussian-mixture lights, "
-                                   "64x64 blue-noise tile, ~64 accepted/eye",
-                       "n_eyes": n_e, "n_lights": n_l, "tau": tau, "tree_height": height,
-                       "step": "build light tree + cull all eyes", "topology": TOPOLOGY,
-                       "l2": "flushed between steps (512 MiB write outside the step events)",
-                       "parallelism": f"replicas x{ws}"},
+            "config": frame_config(args, n_e, n_l, tau, height, ws),
             "accepted_pairs": int(cnt), "accepted_per_eye": cnt / n_e, "node_visits": int(V),
             "cull_only": {"ms": cull_ms, "value": n_e * n_l / (cull_ms / 1e3), "unit": UNIT},
             "refit": refit,
@@ -697,6 +692,16 @@ def cpu_baseline(s, target_seconds=15.0):
                       f"{n_e} eyes"}
 
 
+def frame_config(args, n_e, n_l, tau, height, ws):
+    """The benchmark workload's description, the same for both arms."""
+    return {"workload": f"frame {args.eyes} eyes x {n_l} Gaussian-mixture lights, "
+                        "64x64 blue-noise tile, ~64 accepted/eye",
+            "n_eyes": n_e, "n_lights": n_l, "tau": tau, "tree_height": height,
+            "step": "build light tree + cull all eyes", "topology": TOPOLOGY,
+            "l2": "flushed between steps (512 MiB write outside the step events)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     """The oracle as the reference arm: each step culls a bounded eye sample on the host."""
     import numpy as np
@@ -724,9 +729,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/f32",
             "data": "synthetic",
-            "config": {"workload": f"frame {args.eyes} eyes x {n_l} Gaussian-mixture lights, "
-                                   "64x64 blue-noise tile, ~64 accepted/eye",
-                       "n_eyes": n_e, "n_lights": n_l, "tau": float(s.tau)},
+            "config": frame_config(args, n_e, n_l, float(s.tau), int(tree.height), ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
                              "sample": f"{n} evenly spaced eyes x all {n_l} lights per step "
                                        f"(hierarchical oracle; tree built once in {t_build:.2f} s)"},
