@@ -75,34 +75,20 @@ __global__ void __launch_bounds__(kThreads) radix_hist_kernel(const uint64_t *__
     hist[(uint64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive prefix sum, in place, of the digit-major histogram hist[d * nblocks + b]
-// (256 digits): one block; a warp scans one digit's row at a time (coalesced, with a
-// running carry), then one warp scans the 256 digit totals and every row adds its base.
-__global__ void __launch_bounds__(1024) exclusive_scan_kernel(uint32_t *hist, uint32_t nblocks) {
-    __shared__ uint32_t base[256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = warp; d < 256; d += 32) {
-        uint32_t *row = hist + (uint64_t)d * nblocks;
-        uint32_t carry = 0;
-        for (uint32_t b0 = 0; b0 < nblocks; b0 += 32) {
-            const uint32_t b = b0 + lane;
-            const uint32_t v = b < nblocks ? row[b] : 0u;
-            uint32_t x = v;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (b < nblocks) row[b] = carry + x - v;
-            carry += __shfl_sync(0xFFFFFFFFu, x, 31);
-        }
-        if (lane == 0) base[d] = carry;
-    }
-    __syncthreads();
-    if (warp == 0) {
+// Exclusive prefix sums of each digit's row of the digit-major histogram
+// hist[d * nblocks + b] (256 digits), in place, one warp per digit (8 consecutive counts per
+// lane, a running carry over chunks of 256), and each digit's total in totals[d].
+__global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t *hist, uint32_t nblocks, uint32_t *totals) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t d = blockIdx.x * 8u + (threadIdx.x >> 5);
+    uint32_t *row = hist + (uint64_t)d * nblocks;
+    uint32_t carry = 0;
+    for (uint32_t b0 = 0; b0 < nblocks; b0 += 256) {
+        const uint32_t base = b0 + (uint32_t)lane * 8u;
         uint32_t v[8], s = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            v[k] = base[lane * 8 + k];
+            v[k] = base + k < nblocks ? row[base + k] : 0u;
             s += v[k];
         }
         uint32_t x = s;
@@ -110,19 +96,15 @@ __global__ void __launch_bounds__(1024) exclusive_scan_kernel(uint32_t *hist, ui
             const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
             if (lane >= o) x += y;
         }
-        uint32_t run = x - s;
+        uint32_t run = carry + x - s;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            base[lane * 8 + k] = run;
+            if (base + k < nblocks) row[base + k] = run;
             run += v[k];
         }
+        carry += __shfl_sync(0xFFFFFFFFu, x, 31);
     }
-    __syncthreads();
-    for (int d = warp; d < 256; d += 32) {
-        uint32_t *row = hist + (uint64_t)d * nblocks;
-        const uint32_t add = base[d];
-        for (uint32_t b = lane; b < nblocks; b += 32) row[b] += add;
-    }
+    if (lane == 0) totals[d] = carry;
 }
 
 // Stable scatter of one tile: items are taken 256 at a time in tile order; an item's
@@ -131,11 +113,25 @@ __global__ void __launch_bounds__(1024) exclusive_scan_kernel(uint32_t *hist, ui
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, uint32_t n, int shift,
-    const uint32_t *__restrict__ offsets, uint32_t nblocks) {
+    const uint32_t *__restrict__ offsets, uint32_t nblocks, const uint32_t *__restrict__ totals) {
+    static_assert(kThreads == 256, "one digit per thread");
     __shared__ uint32_t running[256];
     __shared__ uint32_t warp_cnt[kThreads / 32][256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    running[threadIdx.x] = offsets[(uint64_t)threadIdx.x * nblocks + blockIdx.x];
+    {  // the digit's base: exclusive prefix of the digit totals (a block scan)
+        const uint32_t t = totals[threadIdx.x];
+        uint32_t x = t;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) running[warp] = x;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += running[w];
+        __syncthreads();
+        running[threadIdx.x] = offsets[(uint64_t)threadIdx.x * nblocks + blockIdx.x] + before + x - t;
+    }
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) warp_cnt[w][threadIdx.x] = 0;
     __syncthreads();
@@ -931,7 +927,7 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
         tree->height = 0;
     } else {
         const uint32_t nblocks = (n + kTile - 1) / kTile;
-        const uint64_t hist_n = 256ull * nblocks;
+        const uint64_t hist_n = 256ull * (nblocks + 1);  // digit-major counts, then the digit totals
         const size_t bytes = 2 * ((sizeof(uint64_t) * (size_t)n + 255) & ~size_t(255)) +
                              ((sizeof(uint32_t) * (size_t)n + 255) & ~size_t(255)) +
                              ((sizeof(uint32_t) * hist_n + 255) & ~size_t(255)) +
@@ -961,8 +957,9 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
             uint32_t *vin = vals0, *vout = vals1;
             for (int shift = 0; shift < 64; shift += 8) {
                 radix_hist_kernel<<<nblocks, kThreads, 0, st>>>(kin, n, shift, hist, nblocks);
-                exclusive_scan_kernel<<<1, 1024, 0, st>>>(hist, nblocks);
-                radix_scatter_kernel<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n, shift, hist, nblocks);
+                digit_scan_kernel<<<32, 256, 0, st>>>(hist, nblocks, hist + 256 * (size_t)nblocks);
+                radix_scatter_kernel<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n, shift, hist, nblocks,
+                                                                     hist + 256 * (size_t)nblocks);
                 ctx->launches += 3;
                 uint64_t *tk = kin; kin = kout; kout = tk;
                 uint32_t *tv = vin; vin = vout; vout = tv;
@@ -1059,7 +1056,7 @@ constexpr size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t static_scratch_bytes(size_t n) {
     return 2 * pad256(sizeof(uint64_t) * n)                               // keys, ping-pong
            + pad256(sizeof(uint32_t) * n)                                 // second value buffer
-           + pad256(sizeof(uint32_t) * 256 * ((n + kTile - 1) / kTile))   // digit histograms
+           + pad256(sizeof(uint32_t) * 256 * ((n + kTile - 1) / kTile + 1)) // digit histograms, totals
            + pad256(sizeof(float4) * n)                                   // sorted lights
            + 2 * pad256(sizeof(uint32_t) * n)                             // parent links
            + pad256(sizeof(uint32_t) * n)                                 // arrival counters
@@ -1120,7 +1117,7 @@ extern "C" int hrr_build_light_tree_static(hrr_lights L, uint32_t n, hrr_node *d
     char *p = scratch;
     uint64_t *keys0 = carve<uint64_t>(p, kStaticMaxLights), *keys1 = carve<uint64_t>(p, kStaticMaxLights);
     uint32_t *vals1 = carve<uint32_t>(p, kStaticMaxLights);
-    uint32_t *hist = carve<uint32_t>(p, 256 * ((kStaticMaxLights + kTile - 1) / kTile));
+    uint32_t *hist = carve<uint32_t>(p, 256 * ((kStaticMaxLights + kTile - 1) / kTile + 1));
     float4 *spos = carve<float4>(p, kStaticMaxLights);
     uint32_t *leaf_parent = carve<uint32_t>(p, kStaticMaxLights), *int_parent = carve<uint32_t>(p, kStaticMaxLights);
     uint32_t *arrivals = carve<uint32_t>(p, kStaticMaxLights);
@@ -1148,8 +1145,9 @@ extern "C" int hrr_build_light_tree_static(hrr_lights L, uint32_t n, hrr_node *d
             uint32_t *vin = dev_perm, *vout = vals1;
             for (int shift = 0; shift < 64; shift += 8) {
                 radix_hist_kernel<<<nblocks, kThreads, 0, st>>>(kin, n, shift, hist, nblocks);
-                exclusive_scan_kernel<<<1, 1024, 0, st>>>(hist, nblocks);
-                radix_scatter_kernel<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n, shift, hist, nblocks);
+                digit_scan_kernel<<<32, 256, 0, st>>>(hist, nblocks, hist + 256 * (size_t)nblocks);
+                radix_scatter_kernel<<<nblocks, kThreads, 0, st>>>(kin, vin, kout, vout, n, shift, hist, nblocks,
+                                                                     hist + 256 * (size_t)nblocks);
                 uint64_t *tk = kin; kin = kout; kout = tk;
                 uint32_t *tv = vin; vin = vout; vout = tv;
             }
