@@ -200,7 +200,9 @@ def run_ours(args):
     cull_ms = kern_ms / max(kern_n, 1)
     V = statistics.median(visits)
     peaks, kind = _peaks()
-    roof = roofline(V, cnt, n_e, cull_ms, peaks, kind, clk, workload=f"{args.eyes}x{n_l}")
+    measured = ctx.measure_peaks()  # L2, record-fetch and integer denominators (untimed)
+    roof = roofline(V, cnt, n_e, cull_ms, peaks, kind, clk, workload=f"{args.eyes}x{n_l}", n_l=n_l,
+                    measured=measured, tile_bytes=int(np.asarray(s.tile).nbytes))
 
     # end to end through the public API with host buffers
     e2e = None if args.no_e2e else run_e2e(ctx, s, dev, stream, args, cap)
@@ -325,7 +327,7 @@ def aggregate_throughput(units_per_rank: float, t_rank: float, dist=None, device
     return ws * units_per_rank / t, t
 
 
-def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk, workload=""):
+def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk, workload="", n_l=0, measured=None, tile_bytes=0):
     """Roofline of the traversal kernel, which is bound by instruction issue: the node
     records (64 B per visit) stay in L2 and DRAM traffic is essentially the output.
     achieved = algorithmic ops per launch (node visits x OPS_PER_VISIT) / kernel time;
@@ -350,7 +352,34 @@ def roofline(V, accepted, n_e, cull_ms, peaks, kind, clk, workload=""):
         "ops_per_visit": OPS_PER_VISIT,
         "node_visits_per_s": V / sec,
         "node_record_bytes_gbs": 64.0 * V / sec / 1e9,
+        "fractions": other_fractions(V, accepted, n_e, n_l, sec, peaks, measured or {}, tile_bytes),
     }
+
+
+def other_fractions(V, accepted, n_e, n_l, sec, peaks, measured, tile_bytes):
+    """The traversal's other rooflines, against denominators measured on this GPU:
+    - l2: node-record bytes (64 B per visit) against an L2 streaming read, and visits
+      against scattered 64-byte record fetches (two 256-bit loads each, the same form);
+    - hbm: the bytes that must cross HBM once (records 64 (N_l - 1), eyes 16 N_e, the tile,
+      pairs 8 |A|) against the measured copy bandwidth;
+    - int32: the algorithmic ops per visit against independent 32-bit op chains."""
+    out = {}
+    if measured.get("l2_read_gbs"):
+        ach = 64.0 * V / sec / 1e9
+        out["l2_stream"] = {"achieved_gbs": ach, "peak_gbs": measured["l2_read_gbs"],
+                            "frac": ach / measured["l2_read_gbs"]}
+    if measured.get("record_fetches_per_s"):
+        out["record_fetch"] = {"achieved_per_s": V / sec, "peak_per_s": measured["record_fetches_per_s"],
+                               "frac": V / sec / measured["record_fetches_per_s"]}
+    if peaks.get("hbm_gbs"):
+        unique = 64.0 * max(n_l - 1, 1) + 16.0 * n_e + tile_bytes + 8.0 * accepted
+        out["hbm"] = {"unique_bytes": unique, "achieved_gbs": unique / sec / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                      "frac": unique / sec / 1e9 / peaks["hbm_gbs"]}
+    if measured.get("int_ops_per_s"):
+        ach = V * OPS_PER_VISIT / sec
+        out["int32"] = {"achieved_per_s": ach, "peak_per_s": measured["int_ops_per_s"],
+                        "frac": ach / measured["int_ops_per_s"]}
+    return out
 
 
 def run_e2e(ctx, s, dev, stream, args, cap):

@@ -90,6 +90,10 @@ class hrr_cull_opts(C.Structure):
                 ("sample_index", C.c_uint32)]
 
 
+class hrr_peaks(C.Structure):
+    _fields_ = [("l2_read_gbs", C.c_double), ("record_fetches_per_s", C.c_double), ("int_ops_per_s", C.c_double)]
+
+
 class hrr_build_opts(C.Structure):
     _fields_ = [("topology", C.c_int), ("cost_depth", C.c_uint32)]
 
@@ -139,6 +143,7 @@ _SIGS = {
     "hrr_cull_host": (_i32, [_P, hrr_eyes, _u32, _P, _f32, C.POINTER(hrr_cull_opts), _P, _u64,
                              C.POINTER(_u64)]),
     "hrr_last_cull_stats": (_i32, [_P, C.POINTER(_u64), C.POINTER(_u64)]),
+    "hrr_measure_peaks": (_i32, [_P, C.POINTER(hrr_peaks)]),
     "hrr_range_min": (_i32, [_P, _P, _P, _P, _P, _P, _u64, _i32]),
     "hrr_build_light_tree_static": (_i32, [hrr_lights, _u32, _P, _P, C.POINTER(_u32), _P,
                                            C.c_char_p, C.c_size_t]),
@@ -306,6 +311,14 @@ class Context:
         if st not in (HRR_OK, HRR_ERR_OVERFLOW):
             self.check(st)
         return st, int(cnt.value)
+
+    def measure_peaks(self) -> dict:
+        """Measured L2 streaming-read GB/s, scattered 64-byte record fetches/s and 32-bit
+        integer ops/s of this GPU (roofline denominators)."""
+        p = hrr_peaks()
+        self.check(hrr_measure_peaks(self.handle, C.byref(p)))
+        return {"l2_read_gbs": p.l2_read_gbs, "record_fetches_per_s": p.record_fetches_per_s,
+                "int_ops_per_s": p.int_ops_per_s}
 
     def last_cull_stats(self):
         v, a = _u64(), _u64()

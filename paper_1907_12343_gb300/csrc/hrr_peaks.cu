@@ -1,0 +1,151 @@
+// Microbenchmarks for the roofline denominators that a copy and a GEMM do not give: the
+// L2 streaming-read bandwidth, the rate of scattered 64-byte record fetches from L2 (the
+// node fetch of the traversal), and the 32-bit integer operation rate. Measurement only:
+// nothing on the culling path calls them.
+#include <cstdint>
+#include <cstdio>
+
+#include "hrr_internal.cuh"
+
+namespace {
+
+constexpr int kPeakThreads = 256;
+
+// Streams buf (n16 16-byte vectors, L2-resident) reps times with 128-bit loads that bypass
+// L1; the XOR keeps every load live.
+__global__ void __launch_bounds__(kPeakThreads) l2_stream_kernel(const uint4 *__restrict__ buf, uint32_t n16, int reps,
+                                                                 uint32_t *sink) {
+    uint32_t acc = 0;
+    const uint32_t stride = gridDim.x * kPeakThreads;
+    for (int r = 0; r < reps; ++r) {
+        for (uint32_t i = blockIdx.x * kPeakThreads + threadIdx.x; i < n16; i += stride) {
+            const uint4 v = __ldcg(&buf[i]);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    }
+    if (acc == 0x9E3779B9u) sink[0] = acc;  // practically never; the loads stay
+}
+
+// Each lane fetches iters 64-byte records at pseudo-random indices of an L2-resident array
+// of n_rec records (a power of two), as two 256-bit read-only loads, the traversal's form.
+__global__ void __launch_bounds__(kPeakThreads) record_fetch_kernel(const float4 *__restrict__ rec, uint32_t n_rec,
+                                                                    int iters, uint32_t seed, float *sink) {
+    uint32_t x = seed ^ ((blockIdx.x * kPeakThreads + threadIdx.x) * 0x9E3779B9u);
+    float acc = 0.f;
+    for (int k = 0; k < iters; ++k) {
+        x = x * 1664525u + 1013904223u;  // LCG step
+        const float4 *p = rec + 4 * (size_t)((x >> 7) & (n_rec - 1));
+        float a0, a1, a2, a3, a4, a5, a6, a7, b0, b1, b2, b3, b4, b5, b6, b7;
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=f"(a0), "=f"(a1), "=f"(a2), "=f"(a3), "=f"(a4), "=f"(a5), "=f"(a6), "=f"(a7)
+                     : "l"(p));
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
+                     : "=f"(b0), "=f"(b1), "=f"(b2), "=f"(b3), "=f"(b4), "=f"(b5), "=f"(b6), "=f"(b7)
+                     : "l"(p));
+        acc += (((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7))) + (((b0 + b1) + (b2 + b3)) + ((b4 + b5) + (b6 + b7)));
+    }
+    if (acc == 1.2345678f) sink[0] = acc;
+}
+
+// Eight independent chains per thread, each step one 3-input logic op and one add
+// (lop3 then add.u32: they cannot merge into one instruction).
+__global__ void __launch_bounds__(kPeakThreads) int_ops_kernel(uint32_t seed, int iters, uint32_t *sink) {
+    uint32_t a[8];
+    const uint32_t t = blockIdx.x * kPeakThreads + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = seed + t * (2u * j + 1u);
+    const uint32_t b = seed * 0x85EBCA6Bu, c = seed ^ 0xC2B2AE35u;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a[j]) : "r"(b), "r"(c));
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(a[j]) : "r"(c));
+        }
+    }
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s ^= a[j];
+    if (s == 0x9E3779B9u) sink[0] = s;
+}
+
+// Best (shortest) of `runs` timed launches of fn on the context stream, in milliseconds.
+template <typename F>
+int best_ms(hrr_ctx *ctx, int runs, F fn, float *out) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    HRR_CUDA(ctx, cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return hrr_fail(ctx, HRR_ERR_CUDA, "event creation");
+    }
+    float best = 3.4e38f;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r <= runs && e == cudaSuccess; ++r) {  // the first run warms up
+        e = cudaEventRecord(a, ctx->stream);
+        if (e == cudaSuccess) {
+            fn();
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && r > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return hrr_cuda_fail(ctx, e, "peak measurement");
+    *out = best;
+    return HRR_OK;
+}
+
+}  // namespace
+
+extern "C" int hrr_measure_peaks(hrr_ctx *ctx, hrr_peaks *out) {
+    if (!ctx) return HRR_ERR_INVALID_ARG;
+    if (!out) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out is NULL");
+    DeviceGuard g(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t bytes = size_t(64) << 20;  // 2^20 records of 64 B; well inside the L2
+    void *buf = nullptr;
+    uint32_t *sink = nullptr;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess || cudaMalloc(&sink, 64) != cudaSuccess) {
+        cudaGetLastError();
+        if (buf) cudaFree(buf);
+        return hrr_fail(ctx, HRR_ERR_OOM, "peak measurement buffers");
+    }
+    int rc = HRR_OK;
+    do {
+        const cudaError_t e = cudaMemsetAsync(buf, 0x3C, bytes, st);  // finite floats everywhere
+        if (e != cudaSuccess) {
+            rc = hrr_cuda_fail(ctx, e, "peak buffer fill");
+            break;
+        }
+        const unsigned grid = (unsigned)ctx->sm_count * 8u;
+        const uint32_t n16 = (uint32_t)(bytes / 16);
+        const int reps = 16;
+        float ms = 0.f;
+        if ((rc = best_ms(ctx, 3, [&] {
+                 l2_stream_kernel<<<grid, kPeakThreads, 0, st>>>(static_cast<const uint4 *>(buf), n16, reps, sink);
+             }, &ms)) != HRR_OK)
+            break;
+        out->l2_read_gbs = (double)bytes * reps / (ms * 1e-3) / 1e9;
+        const uint32_t n_rec = (uint32_t)(bytes / 64);
+        const int iters = 256;
+        if ((rc = best_ms(ctx, 3, [&] {
+                 record_fetch_kernel<<<grid, kPeakThreads, 0, st>>>(static_cast<const float4 *>(buf), n_rec, iters, 12345u,
+                                                                    reinterpret_cast<float *>(sink));
+             }, &ms)) != HRR_OK)
+            break;
+        out->record_fetches_per_s = (double)grid * kPeakThreads * iters / (ms * 1e-3);
+        const int int_iters = 4096;
+        if ((rc = best_ms(ctx, 3, [&] { int_ops_kernel<<<grid, kPeakThreads, 0, st>>>(7u, int_iters, sink); }, &ms)) !=
+            HRR_OK)
+            break;
+        out->int_ops_per_s = (double)grid * kPeakThreads * int_iters * 16.0 / (ms * 1e-3);
+        ctx->launches += 12;
+    } while (0);
+    cudaStreamSynchronize(st);
+    cudaFree(buf);
+    cudaFree(sink);
+    return rc;
+}
