@@ -47,16 +47,21 @@ def _lights(pos, inten):
 
 
 @pytest.mark.parametrize("case", ["n2", "n3", "n33", "n257", "n1000", "n1025", "n5000", "n100003", "n600001",
-                                  "duplicates", "dark", "chain", "depth1", "depth3"])
+                                  "n4194304", "duplicates", "dark", "chain", "depth1", "depth3"])
 def test_cost_tree_equals_oracle(ctx, case):
     # 33 / 257 / 1025 lights: the first range of each split kernel (warp run of 8, one tile,
     # two tiles); 600001 lights: 587 tiles at the root, scanned in three block passes;
-    # depth1 / depth3: radix splits below a shallow cost depth
+    # depth1 / depth3: radix splits below a shallow cost depth; 2^22 lights: the largest
+    # light set of the batched workload
     n = {"n2": 2, "n3": 3, "n33": 33, "n257": 257, "n1000": 1000, "n1025": 1025, "n5000": 5000,
-         "n100003": 100003, "n600001": 600001}.get(case, 20000)
+         "n100003": 100003, "n600001": 600001, "n4194304": 1 << 22}.get(case, 20000)
     depth = {"depth1": 1, "depth3": 3}.get(case, 0)
-    s = synth.scene_frame(width=8, height=8, n_lights=n, seed=101)
-    pos, inten = s.light_pos.copy(), s.intensity.copy()
+    if n > 1 << 20:  # the frame recipe's lights and intensities, without its tau calibration
+        pos = synth.gaussian_mixture_lights(n, 64, 101)
+        inten = np.exp(1.5 * synth.normal(101, 21, n)).astype(np.float32)
+    else:
+        s = synth.scene_frame(width=8, height=8, n_lights=n, seed=101)
+        pos, inten = s.light_pos.copy(), s.intensity.copy()
     if case == "duplicates":
         pos = np.repeat(pos[:2500], 8, axis=0)
     if case == "dark":
