@@ -210,6 +210,7 @@ def run_ours(args):
     refit = run_refit(ctx, L, dev, stream) if ws == 1 else None
     # the step after the culling: weights and shadow segments of the accepted pairs
     connect = run_connect(ctx, E, L, tau, pairs, cnt, dev, stream) if ws == 1 else None
+    rangemin = run_rangemin(ctx, dev, stream, peaks) if ws == 1 and not args.no_rangemin else None
     del pairs, flush
 
     # the batched (64 uneven frames) and served (Poisson jobs) forms, 1 GPU only
@@ -244,6 +245,7 @@ def run_ours(args):
             "cull_only": {"ms": cull_ms, "value": n_e * n_l / (cull_ms / 1e3), "unit": UNIT},
             "refit": refit,
             "connect": connect,
+            "rangemin": rangemin,
             "wall_s": wall,
             "roofline": roof,
             "e2e": e2e,
@@ -566,6 +568,34 @@ def run_connect(ctx, E, L, tau, pairs, n_pairs, dev, stream, n_tris=1 << 18, rep
             "visibility_value": n_pairs / (m_vis / 1e3), "unit": "connections/s", "visible_fraction": frac}
 
 
+def run_rangemin(ctx, dev, stream, peaks, n=1 << 24, reps=5):
+    """hrr_range_min over n seeded log-uniform (a, b, r) queries, the recipe of the 2^26-query
+    parity workload at 2^24 (335 MB of traffic, well above L2; generating 2^26 on the host
+    takes tens of seconds), inputs resident: median device time of reps launches, and its
+    HBM roofline (20 B per query: a, b, r read, minimum and argmin written)."""
+    import numpy as np
+    import torch
+    import synth
+    a, b, r = synth.rangemin_queries(n, seed=3)
+    ta, tb, tr = (torch.from_numpy(v.view(np.int32)).to(dev) for v in (a, b, r))
+    vmin, karg = torch.empty_like(ta), torch.empty_like(ta)
+    ts = []
+    with torch.cuda.stream(stream):
+        for k in range(reps + 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.range_min(ta, tb, tr, vmin, karg)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    gbs = 20.0 * n / (ms / 1e3) / 1e9
+    hbm = float(peaks.get("hbm_gbs", 0.0)) or None
+    return {"queries": n, "ms": ms, "queries_per_s": n / (ms / 1e3), "bytes_per_query": 20,
+            "achieved_gbs": gbs, "hbm_peak_gbs": hbm, "frac": gbs / hbm if hbm else None}
+
+
 def run_refit(ctx, L, dev, stream, reps=5):
     """Median device time of hrr_refit_light_tree (moved lights, same ids) and of a full
     hrr_build_light_tree over the frame's lights."""
@@ -781,6 +811,7 @@ def main(argv=None):
     ap.add_argument("--topology", choices=["cost", "radix"], default="cost",
                     help="hierarchy shape over the Morton order (the same accepted set)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-rangemin", action="store_true", help="skip the 2^26-query range-minimum leg")
     ap.add_argument("--batch-frames", type=int, default=64, help="0 skips the batched/served forms")
     ap.add_argument("--served-jobs", type=int, default=256, help="0 skips the served form")
     args = ap.parse_args(argv)
