@@ -579,16 +579,23 @@ def run_rangemin(ctx, dev, stream, peaks, n=1 << 24, reps=5):
     a, b, r = synth.rangemin_queries(n, seed=3)
     ta, tb, tr = (torch.from_numpy(v.view(np.int32)).to(dev) for v in (a, b, r))
     vmin, karg = torch.empty_like(ta), torch.empty_like(ta)
+    # a 512 MiB fill before each timed group flushes L2 and keeps the stream busy while the
+    # launches are queued; four back-to-back launches per group (each longer than the
+    # host's launch overhead), so the events time kernels, not launch latency
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    per_group = 4
     ts = []
     with torch.cuda.stream(stream):
         for k in range(reps + 2):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.fill_(k)
             e0.record(stream)
-            ctx.range_min(ta, tb, tr, vmin, karg)
+            for _ in range(per_group):
+                ctx.range_min(ta, tb, tr, vmin, karg)
             e1.record(stream)
             e1.synchronize()
             if k >= 2:
-                ts.append(e0.elapsed_time(e1))
+                ts.append(e0.elapsed_time(e1) / per_group)
     ms = statistics.median(ts)
     gbs = 20.0 * n / (ms / 1e3) / 1e9
     hbm = float(peaks.get("hbm_gbs", 0.0)) or None

@@ -268,15 +268,15 @@ int hrr_last_cull_stats(const hrr_ctx *ctx, uint64_t *visits, uint64_t *accepted
 
 /* Roofline denominators measured on this GPU (not from the paper; measurement only). */
 typedef struct hrr_peaks {
-    double l2_read_gbs;          /* streaming 128-bit reads of a 64 MiB L2-resident buffer */
+    double l2_read_gbs;          /* streaming 128-bit reads of a 32 MiB L2-resident buffer */
     double record_fetches_per_s; /* 64-byte records at random indices of a 64 MiB L2-resident
                                     array, each as two 256-bit loads (the traversal's fetch) */
     double int_ops_per_s;        /* independent 32-bit lop3 / add chains, 8 per thread */
 } hrr_peaks;
 
-/* Run the three microbenchmarks on the context stream (best of three timed launches each,
- * about 10 ms in all) and fill *out. Allocates and frees 64 MiB of device memory.
- * Synchronous. */
+/* Run the three microbenchmarks on the context stream (best of five timed launches of a
+ * few milliseconds each, about 60 ms in all) and fill *out. Allocates and frees 64 MiB of
+ * device memory. Synchronous. */
 int hrr_measure_peaks(hrr_ctx *ctx, hrr_peaks *out);
 
 /* ---- batched culling (many frames in one persistent launch) ---------------------------- */
