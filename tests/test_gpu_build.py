@@ -80,18 +80,26 @@ def test_full_size_frame_lights(ctx):
     _compare(ctx, s.light_pos, s.intensity)
 
 
-def test_nonfinite_lights_rejected(ctx):
+@pytest.mark.parametrize("topology", ["radix", "cost"])
+def test_nonfinite_lights_rejected(ctx, topology):
+    # for the cost-driven build, 5,000 lights reach every split kernel; an infinite
+    # intensity makes the cost of every split of a range holding it NaN (such ranges then
+    # split at their first light down to the cost depth), and the build still ends and
+    # reports the input
     import paper_1907_12343_gb300 as hrr
-    pos = np.random.default_rng(1).random((100, 3)).astype(np.float32)
-    inten = np.ones(100, np.float32)
-    for bad in ("pos", "inten"):
+    n = 5000 if topology == "cost" else 100
+    pos = np.random.default_rng(1).random((n, 3)).astype(np.float32)
+    inten = np.ones(n, np.float32)
+    for bad in ("pos", "inten", "all_nan"):
         p, i = pos.copy(), inten.copy()
         if bad == "pos":
             p[17, 1] = np.nan
-        else:
+        elif bad == "inten":
             i[42] = np.inf
+        else:
+            i[:] = np.nan
         g = upload_scene({"light_pos": p, "intensity": i, "eye_pos": p[:1], "px": np.zeros(1, np.uint16),
                           "py": np.zeros(1, np.uint16)})
         with pytest.raises(hrr.HRRError) as e:
-            ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"])
+            ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"], topology=topology)
         assert e.value.status == hrr.HRR_ERR_INVALID_ARG
