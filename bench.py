@@ -274,12 +274,24 @@ KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
                   for f in ("hrr_cull.cu", "hrr_math.cuh")]
 
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and with whitespace runs collapsed, so that a
+    comment edit does not count as a change of the code (string literals in these sources
+    hold no comment markers)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(files=None) -> str:
+    """Hash of the code (comments and whitespace ignored) of the given sources, by default
+    the traversal kernel's."""
     import hashlib
     h = hashlib.sha256()
     for f in files or KERNEL_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

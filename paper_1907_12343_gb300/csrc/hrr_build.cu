@@ -107,9 +107,9 @@ __global__ void __launch_bounds__(256) digit_scan_kernel(uint32_t *hist, uint32_
     if (lane == 0) totals[d] = carry;
 }
 
-// Stable scatter of one tile: items are taken 256 at a time in tile order; an item's
-// rank among equal digits is (earlier rounds) + (earlier warps this round) + (earlier
-// lanes of its warp, from __match_any_sync).
+// Stable scatter of one tile: items are taken in groups of 256 in tile order; an item's
+// rank among equal digits is (earlier groups) + (earlier warps of its group) + (earlier
+// lanes of its warp, from __match_any_sync); the digit's base comes first.
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
     const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, uint32_t n, int shift,
