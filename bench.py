@@ -211,6 +211,8 @@ def run_ours(args):
     # the step after the culling: weights and shadow segments of the accepted pairs
     connect = run_connect(ctx, E, L, tau, pairs, cnt, dev, stream) if ws == 1 else None
     rangemin = run_rangemin(ctx, dev, stream, peaks) if ws == 1 and not args.no_rangemin else None
+    # several samples per light: psi(n) offsets and a space-time tile
+    samples = run_samples(ctx, s, L, E, px, py, tau, pairs, stream) if ws == 1 else None
     del pairs, flush
 
     # the batched (64 uneven frames) and served (Poisson jobs) forms, 1 GPU only
@@ -246,6 +248,7 @@ def run_ours(args):
             "refit": refit,
             "connect": connect,
             "rangemin": rangemin,
+            "samples": samples,
             "wall_s": wall,
             "roofline": roof,
             "e2e": e2e,
@@ -578,6 +581,44 @@ def run_connect(ctx, E, L, tau, pairs, n_pairs, dev, stream, n_tris=1 << 18, rep
     return {"pairs": int(n_pairs), "weights_ms": m_plain, "weights_value": n_pairs / (m_plain / 1e3),
             "occluders": n_tris, "scene_build_ms": scene_ms, "visibility_ms": m_vis,
             "visibility_value": n_pairs / (m_vis / 1e3), "unit": "connections/s", "visible_fraction": frac}
+
+
+def run_samples(ctx, s, L, E, px, py, tau, pairs, stream, n_samples=4):
+    """Sec. 3's extra samples per light on the frame: sample n culls with the shift
+    r_j + psi(n), psi(n) = n / golden ratio in 32-bit fixed point (a shift offset), and
+    with layer n of a 64 x 64 x n_samples space-time tile. Device time of each cull
+    (library-recorded events) and its accepted pairs."""
+    import synth
+    tree = ctx.build_light_tree(*L, topology=TOPOLOGY)
+    out = {"samples": n_samples}
+    try:
+        for form in ("psi_offset", "spacetime_tile"):
+            if form == "spacetime_tile":
+                ctx.set_shift_tile(synth.shift_tile_3d(64, 64, n_samples, 2))
+            ms, acc = [], []
+            for n in range(n_samples):
+                kw = {"shift_offset": (n * 0x9E3779B9) & 0xFFFFFFFF} if form == "psi_offset" else {"sample_index": n}
+                with torch_stream(stream):
+                    ctx.set_timing(True)
+                    st, cnt = ctx.cull(*E, px, py, tree, tau, pairs, **kw)
+                    t, k = ctx.kernel_time()
+                    ctx.set_timing(False)
+                if st != 0:
+                    raise RuntimeError(f"cull status {st}")
+                ms.append(t / max(k, 1))
+                acc.append(int(cnt))
+            n_e, n_l = int(E[0].numel()), int(L[0].numel())
+            out[form] = {"ms_per_sample": statistics.mean(ms), "accepted_per_sample": acc,
+                         "value": n_e * n_l / (statistics.mean(ms) / 1e3), "unit": UNIT}
+    finally:
+        ctx.set_shift_tile(s.tile)
+        tree.free()
+    return out
+
+
+def torch_stream(stream):
+    import torch
+    return torch.cuda.stream(stream)
 
 
 def run_rangemin(ctx, dev, stream, peaks, n=1 << 24, reps=5):
