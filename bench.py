@@ -586,11 +586,34 @@ def run_connect(ctx, E, L, tau, pairs, n_pairs, dev, stream, n_tris=1 << 18, rep
 def run_samples(ctx, s, L, E, px, py, tau, pairs, stream, n_samples=4):
     """Sec. 3's extra samples per light on the frame: sample n culls with the shift
     r_j + psi(n), psi(n) = n / golden ratio in 32-bit fixed point (a shift offset), and
-    with layer n of a 64 x 64 x n_samples space-time tile. Device time of each cull
-    (library-recorded events) and its accepted pairs."""
+    with layer n of a 64 x 64 x n_samples space-time tile. One cull per sample (device time
+    from library-recorded events) and all samples in one traversal (hrr_cull_samples,
+    CUDA events on the stream), with the accepted pairs of each sample."""
+    import torch
     import synth
     tree = ctx.build_light_tree(*L, topology=TOPOLOGY)
     out = {"samples": n_samples}
+    n_e = int(E[0].numel())
+    fused_pairs = torch.empty((n_samples, 80 * n_e, 2), dtype=torch.int32, device=E[0].device)
+
+    def fused(offsets, reps=3):
+        ts, counts = [], None
+        with torch_stream(stream):
+            for k in range(reps + 1):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                st, counts, vis = ctx.cull_samples(*E, px, py, tree, tau, offsets, fused_pairs)
+                b.record(stream)
+                b.synchronize()
+                if st != 0:
+                    raise RuntimeError(f"cull_samples status {st}")
+                if k:
+                    ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        return {"ms": ms, "ms_per_sample": ms / len(offsets), "accepted_per_sample": counts,
+                "sample_visits": vis[0], "records_fetched": vis[1],
+                "value_per_sample": n_e * int(L[0].numel()) / (ms / len(offsets) / 1e3), "unit": UNIT}
+
     try:
         for form in ("psi_offset", "spacetime_tile"):
             if form == "spacetime_tile":
@@ -607,12 +630,19 @@ def run_samples(ctx, s, L, E, px, py, tau, pairs, stream, n_samples=4):
                     raise RuntimeError(f"cull status {st}")
                 ms.append(t / max(k, 1))
                 acc.append(int(cnt))
-            n_e, n_l = int(E[0].numel()), int(L[0].numel())
+            n_l = int(L[0].numel())
             out[form] = {"ms_per_sample": statistics.mean(ms), "accepted_per_sample": acc,
                          "value": n_e * n_l / (statistics.mean(ms) / 1e3), "unit": UNIT}
+            offs = [(n * 0x9E3779B9) & 0xFFFFFFFF for n in range(n_samples)] if form == "psi_offset" else [0] * n_samples
+            f = fused(offs)
+            if f["accepted_per_sample"] != acc:
+                raise RuntimeError(f"one-traversal samples disagree with per-sample culls: {f['accepted_per_sample']} {acc}")
+            f["speedup_vs_per_sample_culls"] = statistics.mean(ms) * n_samples / f["ms"]
+            out[form]["one_traversal"] = f
     finally:
         ctx.set_shift_tile(s.tile)
         tree.free()
+        del fused_pairs
     return out
 
 

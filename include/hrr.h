@@ -248,6 +248,23 @@ int hrr_cull(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree,
 int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree,
                 float tau, const hrr_cull_opts *opts, uint32_t *dev_pairs, uint64_t cap,
                 uint64_t *out_count);
+/* Several samples per light in one traversal (Sec. 3: n samples per light with shifts
+ * r_j + psi(n), and space-time shifts psi(j, n)). Sample s of eye j uses the shift
+ * tile_s[pixel of j] + offsets[s] (mod 2^32), where tile_s is layer s mod d of the context
+ * tile (the tile itself when it has one layer); its pairs are exactly those hrr_cull_ex
+ * gives with shift_offset = offsets[s] and sample_index = s. One traversal per eye visits
+ * the union of the samples' nodes and fetches each record once. n_samples in [1, 32];
+ * offsets: host array of n_samples. dev_pairs: n_samples * cap pairs (2 uint32 each,
+ * 8-byte aligned), sample s's pairs at dev_pairs + 2 * cap * s, as (eye index, original
+ * light id) in unspecified order. out_counts: host array of n_samples, sample s's count.
+ * out_visits: NULL or a host array of 2: the node visits summed over the samples (equal
+ * to the total of hrr_cull_ex over the samples) and the node records fetched.
+ * HRR_ERR_OVERFLOW if a sample's count exceeds cap (its first cap pairs are written).
+ * Synchronous. */
+int hrr_cull_samples(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
+                     const uint32_t *offsets, uint32_t n_samples, uint32_t *dev_pairs, uint64_t cap,
+                     uint64_t *out_counts, uint64_t *out_visits);
+
 /* hrr_cull with host buffers: the eyes are read from host memory (host_eyes: host SoA,
  * n_eyes entries each) and the accepted pairs written to host memory (host_pairs: 2 * cap
  * uint32), as (eye index, original light id) with the same set as hrr_cull_ex gives for the

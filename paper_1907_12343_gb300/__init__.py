@@ -144,6 +144,7 @@ _SIGS = {
                              C.POINTER(_u64)]),
     "hrr_last_cull_stats": (_i32, [_P, C.POINTER(_u64), C.POINTER(_u64)]),
     "hrr_measure_peaks": (_i32, [_P, C.POINTER(hrr_peaks)]),
+    "hrr_cull_samples": (_i32, [_P, hrr_eyes, _u32, _P, _f32, _P, _u32, _P, _u64, _P, _P]),
     "hrr_range_min": (_i32, [_P, _P, _P, _P, _P, _P, _u64, _i32]),
     "hrr_build_light_tree_static": (_i32, [hrr_lights, _u32, _P, _P, C.POINTER(_u32), _P,
                                            C.c_char_p, C.c_size_t]),
@@ -311,6 +312,24 @@ class Context:
         if st not in (HRR_OK, HRR_ERR_OVERFLOW):
             self.check(st)
         return st, int(cnt.value)
+
+    def cull_samples(self, x, y, z, px, py, tree: "Tree", tau: float, offsets, pairs):
+        """Several samples per light in one traversal: sample s uses the shift offset
+        offsets[s] (and layer s mod d of a space-time tile); ``pairs`` has shape
+        (n_samples, cap, 2). Returns (status, counts per sample, (sample visits, records
+        fetched)). HRR_ERR_OVERFLOW is returned, not raised."""
+        import numpy as np
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64) & 0xFFFFFFFF, dtype=np.uint32)
+        ns = int(off.size)
+        cap = int(pairs.shape[1]) if pairs is not None and pairs.ndim == 3 else 0
+        counts = np.zeros(max(ns, 1), np.uint64)
+        visits = np.zeros(2, np.uint64)
+        E = hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py))
+        st = hrr_cull_samples(self.handle, E, int(x.numel()), tree.handle, float(tau), off.ctypes.data, ns,
+                              _ptr(pairs) if cap else None, cap, counts.ctypes.data, visits.ctypes.data)
+        if st not in (HRR_OK, HRR_ERR_OVERFLOW):
+            self.check(st)
+        return st, [int(c) for c in counts[:ns]], (int(visits[0]), int(visits[1]))
 
     def measure_peaks(self) -> dict:
         """Measured L2 streaming-read GB/s, scattered 64-byte record fetches/s and 32-bit

@@ -110,6 +110,7 @@ int hrr_destroy(hrr_ctx *ctx) {
     if (ctx->host_eyes_dev) cudaFree(ctx->host_eyes_dev);
     if (ctx->host_pairs_dev) cudaFree(ctx->host_pairs_dev);
     if (ctx->slice_counters) cudaFree(ctx->slice_counters);
+    if (ctx->sample_counters) cudaFree(ctx->sample_counters);
     if (ctx->ev_first) cudaEventDestroy(ctx->ev_first);
     for (int i = 0; i < HRR_HOST_SLICES; ++i) {
         if (ctx->ev_in[i]) cudaEventDestroy(ctx->ev_in[i]);
@@ -288,6 +289,27 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
 int hrr_cull(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
              uint32_t *dev_pairs, uint64_t cap, uint64_t *out_count) {
     return hrr_cull_ex(ctx, eyes, n_eyes, tree, tau, nullptr, dev_pairs, cap, out_count);
+}
+
+int hrr_cull_samples(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
+                     const uint32_t *offsets, uint32_t n_samples, uint32_t *dev_pairs, uint64_t cap,
+                     uint64_t *out_counts, uint64_t *out_visits) {
+    if (!ctx) return HRR_ERR_INVALID_ARG;
+    if (!out_counts) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out_counts is NULL");
+    if (n_samples < 1 || n_samples > 32) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "n_samples must be in [1, 32]");
+    for (uint32_t s = 0; s < n_samples; ++s) out_counts[s] = 0;
+    if (!offsets) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "offsets is NULL");
+    if (!tree) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tree is NULL");
+    if (tree->device != ctx->device) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tree lives on another device");
+    if (!(tau >= 0.0f) || !std::isfinite(tau)) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "tau must be finite and >= 0");
+    if (n_eyes > 0 && (!eyes.x || !eyes.y || !eyes.z || !eyes.px || !eyes.py))
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "an eye array is NULL");
+    if (cap > 0 && !dev_pairs) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "dev_pairs is NULL");
+    if (cap > (~0ull / 8) / 32) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "cap too large");
+    if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
+    DeviceGuard g(ctx->device);
+    return hrr_cull_samples_impl(ctx, eyes, n_eyes, tree, tau, offsets, n_samples, dev_pairs, cap, out_counts,
+                                 out_visits);
 }
 
 int hrr_cull_host(hrr_ctx *ctx, hrr_eyes host_eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,

@@ -48,6 +48,7 @@ struct hrr_ctx {
     cudaEvent_t ev_first = nullptr;
     cudaEvent_t ev_in[HRR_HOST_SLICES] = {}, ev_done[HRR_HOST_SLICES] = {}, ev_out[HRR_HOST_SLICES] = {};
     unsigned long long *slice_counters = nullptr;  // device, 4 per slice
+    unsigned long long *sample_counters = nullptr;  // hrr_cull_samples: 40 device counters
     unsigned long long *host_slices = nullptr;     // pinned, 4 per slice
     std::string err;
 };
@@ -157,6 +158,9 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &lights, uint32_t n, hrr_tree 
 int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &eyes, uint32_t n_eyes, const hrr_tree *tree,
                   float tau, const hrr_cull_opts &opts, uint32_t *pairs, uint64_t cap,
                   uint64_t *out_count);
+int hrr_cull_samples_impl(hrr_ctx *ctx, const hrr_eyes &eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
+                          const uint32_t *offsets, uint32_t n_samples, uint32_t *pairs, uint64_t cap,
+                          uint64_t *out_counts, uint64_t *out_visits);
 int hrr_cull_host_impl(hrr_ctx *ctx, const hrr_eyes &host_eyes, uint32_t n_eyes, const hrr_tree *tree,
                        float tau, const hrr_cull_opts &opts, uint32_t *host_pairs, uint64_t cap,
                        uint64_t *out_count);
