@@ -86,6 +86,32 @@ def test_full_size_frame_sampled(ctx):
     assert np.bincount(pairs[:, 0], minlength=n_e).sum() == cnt
 
 
+def test_largest_batch_frame_sampled(ctx):
+    # the largest frame of the batched workload: 1920 x 1080 eyes x 2^22 lights at 128
+    # accepted per eye, over the cost-driven hierarchy; sampled eyes equal the
+    # hierarchical oracle (pairs and visits), and the count stays within the per-eye cap
+    s = synth.scene_frame(width=1920, height=1080, n_lights=1 << 22, target=128.0, seed=41, tau_lights=1 << 18)
+    g = upload_scene(s)
+    ctx.set_shift_tile(s.tile)
+    tree = ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"], topology="cost")
+    import torch
+    n_e = len(s.eye_pos)
+    cap = 300 * n_e
+    pairs = torch.empty((cap, 2), dtype=torch.int32, device=g["ex"].device)
+    vis = torch.zeros(n_e, dtype=torch.int32, device=g["ex"].device)
+    st, cnt = ctx.cull(g["ex"], g["ey"], g["ez"], g["px"], g["py"], tree, float(s.tau), pairs, eye_visits=vis)
+    tree.free()
+    assert st == 0 and 60 * n_e < cnt < cap
+    ids = np.unique(np.concatenate([np.arange(0, n_e, n_e // 151), [n_e - 1]])).astype(np.uint32)
+    sel = pairs[:cnt][torch.isin(pairs[:cnt, 0], torch.from_numpy(ids.astype(np.int32)).to(pairs.device))]
+    got = sel.cpu().numpy().view(np.uint32)
+    del pairs, sel
+    t = oracle.Tree(s.light_pos, s.intensity, topology="cost")
+    hier = oracle.cull_hier(t, s.eye_pos[ids], s.px[ids], s.py[ids], s.tile, s.tau, eye_ids=ids)
+    assert np.array_equal(sorted_pairs(got), sorted_pairs(hier["pairs"]))
+    assert np.array_equal(vis.cpu().numpy().view(np.uint32)[ids], hier["visits"].astype(np.uint32))
+
+
 @pytest.mark.parametrize("n_lights", [1, 2, 3, 33])
 def test_tiny_light_sets(ctx, n_lights):
     s = dict(synth.scene_uniform(n_lights=64, grid_w=16, grid_h=8, tile_w=8, tile_h=8,
