@@ -274,7 +274,7 @@ OPS_PER_VISIT = 1.960 * 27 + 0.973 * 51 + 0.988 * 2 + 0.040 * 17
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_1920x1080.md")
 TOPOLOGY = "cost"  # hierarchy shape of the benchmarked builds (set from --topology)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
-                  for f in ("hrr_cull.cu", "hrr_math.cuh")]
+                  for f in ("hrr_cull_kernel.cuh", "hrr_math.cuh")]
 
 
 def _code_only(text: str) -> str:

@@ -91,7 +91,7 @@ struct DeviceGuard {
     }
 };
 
-// One frame of a traversal launch, as the kernel reads it (hrr_cull.cu): a single frame
+// One frame of a traversal launch, as the kernel reads it (hrr_cull_kernel.cuh): a single frame
 // for hrr_cull, an array of them for batches. 128 bytes.
 struct hrr_cull_frame_t {
     const float *ex, *ey, *ez;
@@ -121,7 +121,7 @@ inline bool hrr_tuning_valid(const hrr_tuning &t) {
     return t.rangemin_variant >= 0 && t.rangemin_variant <= 2 && t.blocks_per_sm <= 64;
 }
 
-// The traversal (hrr_cull.cu). Threads per block of its persistent grid, and frames of one
+// The traversal (hrr_cull_kernel.cuh). Threads per block of its persistent grid, and frames of one
 // batched launch (their descriptors are kernel parameters: 128 x 128 bytes):
 #define HRR_CULL_THREADS 256
 #define HRR_CULL_MAX_FRAMES 128u
