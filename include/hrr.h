@@ -100,9 +100,10 @@ typedef struct hrr_cull_opts {
     /* device pointer to n_eyes uint32, or NULL: receives the number of internal nodes
      * each eye visited (the root counts; a node is visited iff no ancestor culled it) */
     uint32_t *eye_visits;
-    /* range-minimum variant, all with identical results: 0 = closed-form successor search
-     * evaluated without branches (default), 1 = the paper's Alg. 2 with Alg. 3 (with the
-     * a = 0 fallback to Alg. 1), 2 = the closed form with branches */
+    /* range-minimum variant, both with identical results: 0 = closed-form successor search
+     * evaluated without branches (default), 2 = the same closed form with branches. (1 is
+     * not accepted: the paper's Alg. 2 + 3, which the oracle restates, is not built into the
+     * library; it is O(B^2) and 50x slower as a traversal's range minimum.) */
     int rangemin_variant;
     /* added (mod 2^32) to every eye's shift: the sample offset psi(n) of the adaptive
      * sampling variant (Sec. 3), absorbed into the shift; 0 for the plain method */
@@ -211,7 +212,8 @@ int hrr_tree_download(hrr_ctx *ctx, const hrr_tree *tree, hrr_node *host_nodes,
  *     default stream), and synchronises that stream before returning.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, which may load the library's GPU code); make that first
- *     call before any stream capture.
+ *     call before any stream capture. The address is kept for the life of the process:
+ *     after a cudaDeviceReset of a device, do not call this entry point on it again.
  *   - All calls on a device share the array: calls whose GPU work overlaps (for
  *     example on two streams) race and produce garbage. Serialise them.
  *   - err (may be NULL) receives a message of at most err_len bytes on failure. */
@@ -321,7 +323,9 @@ typedef struct hrr_batch hrr_batch; /* opaque, library-owned */
  * their descriptors and per-frame counters to the device and, when use_graph != 0, records
  * the launch (counter reset + one persistent traversal over every frame's eyes) into a
  * CUDA graph. tuning may be NULL (defaults). The frames' memory must stay valid while the
- * batch exists. Synchronous.
+ * batch exists. Frames without a tile read the context's tile as it is now: the batch keeps
+ * a reference to it, so a later hrr_set_shift_tile does not change (or free) what the batch
+ * reads. Destroy a batch before its context. Synchronous.
  * Status HRR_ERR_NO_TILE if a frame has no tile and the context has none. */
 int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames,
                      const hrr_tuning *tuning, int use_graph, hrr_batch **out);
@@ -341,7 +345,10 @@ int hrr_cull_batch(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames,
 /* ---- served culling (continuous batching) --------------------------------------------- */
 
 /* A culling job: eyes against a device-resident hierarchy and tile. The server reserves
- * cap output pairs for it. All pointers must stay valid until the job is released. */
+ * cap output pairs for it. All pointers must stay valid until the job is released. A job
+ * without a tile reads the submitting context's tile as it is at submission; the job keeps
+ * a reference to it until hrr_server_release, so a later hrr_set_shift_tile on that
+ * context does not change (or free) the job's tile. */
 typedef struct hrr_job {
     hrr_eyes eyes;              /* device SoA */
     uint32_t n_eyes;
@@ -445,13 +452,13 @@ int hrr_connect(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, hrr_lights lights,
                 float tau, const uint32_t *dev_pairs, uint64_t n_pairs, const hrr_scene *scene,
                 float *dev_weight, uint8_t *dev_visible, float *dev_eye_sum);
 
-/* ---- range minimum (Sec. 2, Alg. 1-3) -------------------------------------------------- */
+/* ---- range minimum (Sec. 2) ----------------------------------------------------------- */
 
 /* For q in [0, n): out_min[q] = min_{i in [a[q], b[q])} (brev32(i) + r[q]) mod 2^32 and
  * out_argmin[q] = the unique index attaining it (v(a,b) and k of Sec. 1-2 in 32-bit fixed
  * point). Device pointers; out_argmin may be NULL. An empty range (a >= b) gives
- * out_min = 0xFFFFFFFF and out_argmin = 0xFFFFFFFF. variant (0, 1 or 2) as in
- * hrr_cull_opts.
+ * out_min = 0xFFFFFFFF and out_argmin = 0xFFFFFFFF. variant (0 or 2) as in
+ * hrr_cull_opts; any other value is HRR_ERR_INVALID_ARG.
  * Asynchronous (no stream synchronisation). */
 int hrr_range_min(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r,
                   uint32_t *out_min, uint32_t *out_argmin, uint64_t n, int variant);

@@ -26,20 +26,25 @@ CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fround
           "-fno-fast-math", "-Wall", "-Wno-unknown-pragmas"]
 
 
-def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` (with OpenMP when the compiler has it)."""
-    os.makedirs(_OUT_DIR, exist_ok=True)
+def build(force: bool = False, openmp: bool = True, out: str | None = None) -> str:
+    """Compile ``liboracle.so`` (with OpenMP when asked for and the compiler has it; the
+    plain C99 build without it is single-threaded). ``out`` names another library file."""
+    lib_path = out or _LIB
+    os.makedirs(os.path.dirname(lib_path), exist_ok=True)
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
-        return _LIB
-    tmp = _LIB + f".tmp{os.getpid()}"
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= newest:
+        return lib_path
+    tmp = lib_path + f".tmp{os.getpid()}"
     base = ["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"]
-    try:
-        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
-    except subprocess.CalledProcessError:
-        subprocess.run(base, check=True, capture_output=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    if openmp:
+        try:
+            subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+        except subprocess.CalledProcessError:
+            subprocess.run(base, check=True, capture_output=True)
+    else:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 class _Result(C.Structure):
@@ -72,54 +77,58 @@ class _Tree(C.Structure):
     ]
 
 
+def configure(L):
+    """Set the argument and result types of an oracle library's functions (any build)."""
+    u32, u64, f32, i32 = C.c_uint32, C.c_uint64, C.c_float, C.c_int
+    P = C.c_void_p
+    L.or_brev.restype = u32
+    L.or_brev.argtypes = [u32, i32]
+    for nm in ("or_rangemin_scan", "or_rangemin_trie"):
+        getattr(L, nm).restype = u32
+        getattr(L, nm).argtypes = [u64, u64, u32, i32, C.POINTER(u64)]
+    L.or_alg1.restype = u64
+    L.or_alg1.argtypes = [u64, u64, i32]
+    for nm in ("or_alg2_printed", "or_alg2_fixed"):
+        getattr(L, nm).restype = u64
+        getattr(L, nm).argtypes = [u64, u64, u32, i32]
+    L.or_rangemin_batch.restype = None
+    L.or_rangemin_batch.argtypes = [P, P, P, u64, i32, i32, P, P, i32]
+    L.or_fround.restype = f32
+    L.or_fround.argtypes = [i32, f32, f32, i32]
+    L.or_leaf_threshold.restype = u64
+    L.or_leaf_threshold.argtypes = [f32, P, f32, P]
+    L.or_node_culls.restype = i32
+    L.or_node_culls.argtypes = [f32, P, P, f32, P, u32]
+    L.or_morton.restype = u64
+    L.or_morton.argtypes = [f32, f32, f32]
+    L.or_tree_build.restype = C.POINTER(_Tree)
+    L.or_tree_build.argtypes = [P, P, u32]
+    L.or_tree_build_cost.restype = C.POINTER(_Tree)
+    L.or_tree_build_cost.argtypes = [P, P, u32, u32]
+    L.or_tree_free.restype = None
+    L.or_tree_free.argtypes = [C.POINTER(_Tree)]
+    L.or_tree_refit.restype = None
+    L.or_tree_refit.argtypes = [C.POINTER(_Tree), P, P]
+    for nm in ("or_cull_flat", "or_cull_hier"):
+        getattr(L, nm).restype = C.POINTER(_Result)
+        getattr(L, nm).argtypes = [C.POINTER(_Tree), P, P, P, P, u32, P, u32, u32, f32, i32]
+    L.or_cull_free.restype = None
+    L.or_cull_free.argtypes = [C.POINTER(_Result)]
+    L.or_max_threads.restype = i32
+    L.or_pair_weight.restype = None
+    L.or_pair_weight.argtypes = [f32, P, f32, P, P, P]
+    L.or_segment_hits.restype = i32
+    L.or_segment_hits.argtypes = [P, P, P]
+    L.or_connect.restype = None
+    L.or_connect.argtypes = [P, u32, P, P, P, u64, f32, P, u32, P, P, P, i32]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            u32, u64, f32, i32 = C.c_uint32, C.c_uint64, C.c_float, C.c_int
-            P = C.c_void_p
-            L.or_brev.restype = u32
-            L.or_brev.argtypes = [u32, i32]
-            for nm in ("or_rangemin_scan", "or_rangemin_trie"):
-                getattr(L, nm).restype = u32
-                getattr(L, nm).argtypes = [u64, u64, u32, i32, C.POINTER(u64)]
-            L.or_alg1.restype = u64
-            L.or_alg1.argtypes = [u64, u64, i32]
-            for nm in ("or_alg2_printed", "or_alg2_fixed"):
-                getattr(L, nm).restype = u64
-                getattr(L, nm).argtypes = [u64, u64, u32, i32]
-            L.or_rangemin_batch.restype = None
-            L.or_rangemin_batch.argtypes = [P, P, P, u64, i32, i32, P, P, i32]
-            L.or_fround.restype = f32
-            L.or_fround.argtypes = [i32, f32, f32, i32]
-            L.or_leaf_threshold.restype = u64
-            L.or_leaf_threshold.argtypes = [f32, P, f32, P]
-            L.or_node_culls.restype = i32
-            L.or_node_culls.argtypes = [f32, P, P, f32, P, u32]
-            L.or_morton.restype = u64
-            L.or_morton.argtypes = [f32, f32, f32]
-            L.or_tree_build.restype = C.POINTER(_Tree)
-            L.or_tree_build.argtypes = [P, P, u32]
-            L.or_tree_build_cost.restype = C.POINTER(_Tree)
-            L.or_tree_build_cost.argtypes = [P, P, u32, u32]
-            L.or_tree_free.restype = None
-            L.or_tree_free.argtypes = [C.POINTER(_Tree)]
-            L.or_tree_refit.restype = None
-            L.or_tree_refit.argtypes = [C.POINTER(_Tree), P, P]
-            for nm in ("or_cull_flat", "or_cull_hier"):
-                getattr(L, nm).restype = C.POINTER(_Result)
-                getattr(L, nm).argtypes = [C.POINTER(_Tree), P, P, P, P, u32, P, u32, u32, f32, i32]
-            L.or_cull_free.restype = None
-            L.or_cull_free.argtypes = [C.POINTER(_Result)]
-            L.or_max_threads.restype = i32
-            L.or_pair_weight.restype = None
-            L.or_pair_weight.argtypes = [f32, P, f32, P, P, P]
-            L.or_segment_hits.restype = i32
-            L.or_segment_hits.argtypes = [P, P, P]
-            L.or_connect.restype = None
-            L.or_connect.argtypes = [P, u32, P, P, P, u64, f32, P, u32, P, P, P, i32]
-            _lib = L
+            _lib = configure(C.CDLL(build()))
     return _lib
 
 

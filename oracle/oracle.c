@@ -314,7 +314,6 @@ static float sub_rd(float x, float y) { return or_fround(1, x, y, -1); }
 static float add_rd(float x, float y) { return or_fround(0, x, y, -1); }
 static float mul_rd(float x, float y) { return or_fround(2, x, y, -1); }
 static float mul_ru(float x, float y) { return or_fround(2, x, y, +1); }
-static float div_ru(float x, float y) { return or_fround(3, x, y, +1); }
 
 /* ------------------------------------------------------------------------------------ */
 /* Acceptance thresholds                                                                  */
@@ -934,9 +933,9 @@ void or_connect(const float *eye_pos, uint32_t n_eyes, const float *light_pos, c
                 const uint32_t *pairs, uint64_t n_pairs, float tau, const float *tris, uint32_t n_tri,
                 float *weight, uint8_t *visible, double *eye_sum, int nthreads)
 {
-    if (nthreads > 0)
-        omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 256)
+    int nt = pick_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 256) num_threads(nt)
     for (int64_t k = 0; k < (int64_t)n_pairs; ++k) {
         uint32_t j = pairs[2 * k], id = pairs[2 * k + 1];
         const float *e = &eye_pos[3 * (uint64_t)j], *l = &light_pos[3 * (uint64_t)id];

@@ -101,7 +101,9 @@ int hrr_destroy(hrr_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     release_events(ctx);
     for (auto e : ctx->ev_pool) cudaEventDestroy(e);
-    if (ctx->tile) cudaFree(ctx->tile);
+    hrr_tile_release(ctx->tile_buf, ctx->stream);  // batches or jobs may still hold it
+    ctx->tile_buf = nullptr;
+    ctx->tile = nullptr;
     if (ctx->counters) cudaFree(ctx->counters);
     if (ctx->host_counters) cudaFreeHost(ctx->host_counters);
     if (ctx->spill) cudaFree(ctx->spill);
@@ -253,7 +255,15 @@ int hrr_set_shift_tile_3d(hrr_ctx *ctx, const uint32_t *host_tile, uint32_t w, u
         cudaFreeAsync(dev, ctx->stream);
         return hrr_cuda_fail(ctx, e, "copy of the shift tile");
     }
-    if (ctx->tile) HRR_CUDA(ctx, cudaFreeAsync(ctx->tile, ctx->stream));
+    hrr_tile_buf *buf = new (std::nothrow) hrr_tile_buf();
+    if (!buf) {
+        cudaFreeAsync(dev, ctx->stream);
+        return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of the tile");
+    }
+    buf->dev = dev;
+    // The old tile lives on while a batch or a served job still holds a reference to it.
+    hrr_tile_release(ctx->tile_buf, ctx->stream);
+    ctx->tile_buf = buf;
     ctx->tile = dev;
     ctx->tile_w = w;
     ctx->tile_h = h;
@@ -280,8 +290,8 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
     if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
     hrr_cull_opts o{};
     if (opts) o = *opts;
-    if (o.rangemin_variant < 0 || o.rangemin_variant > 2 || o.blocks_per_sm > 64)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2 and blocks_per_sm <= 64");
+    if ((o.rangemin_variant != 0 && o.rangemin_variant != 2) || o.blocks_per_sm > 64)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0 or 2 and blocks_per_sm <= 64");
     DeviceGuard g(ctx->device);
     return hrr_cull_impl(ctx, eyes, n_eyes, tree, tau, o, dev_pairs, cap, out_count);
 }
@@ -326,8 +336,8 @@ int hrr_cull_host(hrr_ctx *ctx, hrr_eyes host_eyes, uint32_t n_eyes, const hrr_t
     if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
     hrr_cull_opts o{};
     if (opts) o = *opts;
-    if (o.rangemin_variant < 0 || o.rangemin_variant > 2 || o.blocks_per_sm > 64)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0, 1 or 2 and blocks_per_sm <= 64");
+    if ((o.rangemin_variant != 0 && o.rangemin_variant != 2) || o.blocks_per_sm > 64)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0 or 2 and blocks_per_sm <= 64");
     DeviceGuard g(ctx->device);
     return hrr_cull_host_impl(ctx, host_eyes, n_eyes, tree, tau, o, host_pairs, cap, out_count);
 }
@@ -344,7 +354,7 @@ int hrr_range_min(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint
     if (!ctx) return HRR_ERR_INVALID_ARG;
     if (n == 0) return HRR_OK;
     if (!a || !b || !r || !out_min) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "NULL array");
-    if (variant < 0 || variant > 2) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "variant must be 0, 1 or 2");
+    if (variant != 0 && variant != 2) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "variant must be 0 or 2");
     DeviceGuard g(ctx->device);
     return hrr_range_min_impl(ctx, a, b, r, out_min, out_argmin, n, variant);
 }

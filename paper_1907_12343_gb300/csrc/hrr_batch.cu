@@ -30,6 +30,8 @@ struct hrr_batch {
     std::vector<uint64_t> caps;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
+    hrr_tile_buf *ctx_tile = nullptr;           // the context tile the frames read, if any (a reference)
+    cudaStream_t stream = nullptr;              // the context stream (runs the batch)
 
     size_t n_counters() const { return 2 * (size_t)n_frames + parts.size() + 1; }
 };
@@ -55,6 +57,7 @@ void release(hrr_batch *b) {
     if (b->dev_counts) cudaFree(b->dev_counts);
     if (b->host_counts) cudaFreeHost(b->host_counts);
     if (b->spill) cudaFree(b->spill);
+    hrr_tile_release(b->ctx_tile, b->stream);
     delete b;
 }
 
@@ -77,6 +80,7 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
     b->tuning = hrr_tuning_normalized(tn);
     b->caps.resize(n_frames);
     b->desc.resize(n_frames);
+    b->stream = ctx->stream;
     DeviceGuard g(ctx->device);
     unsigned long long cursor = 0;
     uint32_t height = 0;
@@ -105,6 +109,10 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
             b->parts.push_back(hrr_batch::Part{});
             b->parts.back().first = i;
             cursor = 0;
+        }
+        if (!fr.dev_tile && !b->ctx_tile) {  // keep the context tile alive while the batch exists
+            b->ctx_tile = ctx->tile_buf;
+            hrr_tile_retain(b->ctx_tile);
         }
         hrr_batch::Part &pt = b->parts.back();
         hrr_cull_frame_t &d = b->desc[i];

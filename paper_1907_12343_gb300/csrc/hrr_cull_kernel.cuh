@@ -98,7 +98,9 @@ __device__ __forceinline__ void load_record(const float4 *p, float4 &q0, float4 
 }
 
 // Append the warp's staged pairs to their frames' outputs: one atomic per frame present in
-// each 32-entry chunk (a chunk rarely holds more than one frame).
+// each 32-entry chunk (a chunk rarely holds more than one frame). The pairs are written
+// once and never read by the kernel, so they are stored with the streaming (evict-first)
+// hint: the output stream then does not push the node records out of L2.
 template <bool BATCH>
 __device__ __forceinline__ void flush(const Frame *F, const uint2 *wbuf, const uint16_t *wfr, uint32_t cnt,
                                       int lane) {
@@ -108,7 +110,7 @@ __device__ __forceinline__ void flush(const Frame *F, const uint2 *wbuf, const u
         base = __shfl_sync(0xFFFFFFFFu, base, 0);
         for (uint32_t k = lane; k < cnt; k += 32) {
             const unsigned long long o = base + k;
-            if (o < F[0].cap) F[0].pairs[o] = wbuf[k];
+            if (o < F[0].cap) __stcs(&F[0].pairs[o], wbuf[k]);
         }
     } else {
         for (uint32_t k0 = 0; k0 < cnt; k0 += 32) {
@@ -125,7 +127,7 @@ __device__ __forceinline__ void flush(const Frame *F, const uint2 *wbuf, const u
             if (has) {
                 const Frame &fr = frame_at<BATCH>(F, f);
                 const unsigned long long o = base + rank;
-                if (o < fr.cap) fr.pairs[o] = wbuf[k];
+                if (o < fr.cap) __stcs(&fr.pairs[o], wbuf[k]);
             }
         }
     }
@@ -165,8 +167,7 @@ template <int VARIANT>
 __device__ __forceinline__ uint32_t range_argmin(uint32_t a, uint32_t b, uint32_t r, uint32_t c) {
     uint32_t k;
     if (VARIANT == 0) return hrr_range_argmin_select(a, b, c);
-    if (VARIANT == 1) hrr_rangemin_alg2(a, b, r, &k);
-    else hrr_rangemin_closed(a, b, r, &k);
+    hrr_rangemin_closed(a, b, r, &k);
     return k;
 }
 
@@ -362,12 +363,11 @@ int occupancy() {
 
 template <bool BATCH>
 int occupancy_of(int variant) {
-    return variant == 0 ? occupancy<0, BATCH>() : variant == 1 ? occupancy<1, BATCH>() : occupancy<2, BATCH>();
+    return variant == 0 ? occupancy<0, BATCH>() : occupancy<2, BATCH>();
 }
 
 cudaError_t launch_single(const hrr_tuning &tn, unsigned grid, const Launch &Lc, const Frame &fr, cudaStream_t st) {
     if (tn.rangemin_variant == 0) cull_single_kernel<0><<<grid, kThreads, 0, st>>>(Lc, fr);
-    else if (tn.rangemin_variant == 1) cull_single_kernel<1><<<grid, kThreads, 0, st>>>(Lc, fr);
     else cull_single_kernel<2><<<grid, kThreads, 0, st>>>(Lc, fr);
     return cudaGetLastError();
 }
@@ -375,7 +375,6 @@ cudaError_t launch_single(const hrr_tuning &tn, unsigned grid, const Launch &Lc,
 cudaError_t launch_batch(const hrr_tuning &tn, unsigned grid, const Launch &Lc, const FrameArray<kMaxFrames> &fa,
                          cudaStream_t st) {
     if (tn.rangemin_variant == 0) cull_batch_kernel<0><<<grid, kThreads, 0, st>>>(Lc, fa);
-    else if (tn.rangemin_variant == 1) cull_batch_kernel<1><<<grid, kThreads, 0, st>>>(Lc, fa);
     else cull_batch_kernel<2><<<grid, kThreads, 0, st>>>(Lc, fa);
     return cudaGetLastError();
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -16,11 +17,32 @@
 // Most slices hrr_cull_host splits the eyes into.
 #define HRR_HOST_SLICES 8
 
+// A library-owned shift tile, shared by reference: the context holds one reference, and
+// every batch or served job that reads the context's tile holds another until its GPU
+// work is over. A new hrr_set_shift_tile drops the context's reference only, so a batch's
+// recorded graph or a job in flight keeps reading the tile it was created with.
+struct hrr_tile_buf {
+    uint32_t *dev = nullptr;
+    std::atomic<int> refs{1};
+};
+inline void hrr_tile_retain(hrr_tile_buf *t) {
+    if (t) t->refs.fetch_add(1, std::memory_order_relaxed);
+}
+// Drops one reference; the last one frees the tile, ordered after the work on `st` (every
+// holder releases only once no GPU work of its own reads the tile).
+inline void hrr_tile_release(hrr_tile_buf *t, cudaStream_t st) {
+    if (t && t->refs.fetch_sub(1, std::memory_order_acq_rel) == 1) {
+        if (t->dev) cudaFreeAsync(t->dev, st);
+        delete t;
+    }
+}
+
 struct hrr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // shift tile (library-owned copy)
+    // shift tile (library-owned copy, shared by reference; tile == tile_buf->dev)
+    hrr_tile_buf *tile_buf = nullptr;
     uint32_t *tile = nullptr;
     uint32_t tile_w = 0, tile_h = 0, tile_d = 1;  // d layers of w x h (a space-time tile)
     // device counters of the last cull: [0] accepted pairs, [1] node visits, [2] flags,
@@ -118,7 +140,7 @@ inline hrr_tuning hrr_tuning_of(const hrr_cull_opts &o) {
     return hrr_tuning_normalized(t);
 }
 inline bool hrr_tuning_valid(const hrr_tuning &t) {
-    return t.rangemin_variant >= 0 && t.rangemin_variant <= 2 && t.blocks_per_sm <= 64;
+    return (t.rangemin_variant == 0 || t.rangemin_variant == 2) && t.blocks_per_sm <= 64;
 }
 
 // The traversal (hrr_cull_kernel.cuh). Threads per block of its persistent grid, and frames of one

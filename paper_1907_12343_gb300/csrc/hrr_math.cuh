@@ -118,84 +118,6 @@ __device__ __forceinline__ uint32_t hrr_range_argmin_select(uint32_t a, uint32_t
     return D < L ? c : k;
 }
 
-// The paper's algorithms in 32-bit words (64-bit registers where a step may carry past
-// bit 31). fls = highest set bit, ffs = lowest set bit, both 0-based; ffs(0) = 32.
-__device__ __forceinline__ int hrr_ffs64(uint64_t x) { return x ? __ffsll((long long)x) - 1 : 32; }
-
-// Alg. 1: the index in [a,b) with the most trailing zeros (argmin of the unshifted Phi_2).
-__device__ __forceinline__ uint64_t hrr_alg1(uint64_t a, uint64_t b) {
-    if (a == 0 || a == b - 1) return a;
-    const int b_h = 63 - __clzll((long long)b);
-    const int b_l = __ffsll((long long)a) - 1;
-    uint64_t k = a, m = a;
-    for (int i = b_l; i <= b_h - 1; ++i) {
-        m &= ~(1ull << i);
-        m |= 1ull << (i + 1);
-        if (m >= a && m < b) k = m;
-    }
-    return k;
-}
-
-// Alg. 3: refine(m, i, [a,b)).
-__device__ __forceinline__ uint64_t hrr_refine(uint64_t m, int i, uint64_t a, uint64_t b) {
-    const uint64_t keep = (i >= 64) ? ~0ull : ((1ull << i) - 1ull);
-    i = hrr_ffs64(m & ~keep);
-    while (i < 31) {
-        const uint64_t k = m + (1ull << i);
-        if (k >= a && k < b) m = k;
-        i = hrr_ffs64(m & ~((2ull << i) - 1ull));
-    }
-    return m;
-}
-
-// Alg. 2 (with Alg. 3), followed by the fallback to Alg. 1 that the a = 0 ranges need.
-__device__ __forceinline__ uint32_t hrr_rangemin_alg2(uint32_t a32, uint32_t b32, uint32_t r,
-                                                      uint32_t *argmin) {
-    const uint64_t a = a32, b = b32;
-    const uint32_t T = 0u - r;
-    const uint64_t k_r = __brev(T);
-    uint64_t k = b;
-    bool done = false;
-    if (k_r >= a && k_r < b) {
-        k = k_r;
-        done = true;
-    }
-    if (!done) {
-        const int b_h = 63 - __clzll((long long)b);
-        const int k_p = hrr_ffs64(k_r);
-        uint64_t m = k_r & ((2ull << b_h) - 1ull);
-        for (int i = b_h; i >= k_p && !done; --i) {
-            if ((m >> i) & 1ull) {
-                m &= ~(1ull << i);
-            } else {
-                uint64_t m_i = m | (1ull << i);
-                if (m_i < a) m_i |= 1ull << (i + 1);
-                m_i = hrr_refine(m_i, i + 1, a, b);
-                if (m_i >= a && m_i < b) {
-                    k = m_i;
-                    done = true;
-                }
-            }
-            if ((a >> i) & 1ull) m |= 1ull << i;
-        }
-        if (!done) {
-            m = a;
-            k = b;
-            for (int i = 0; i < 32; ++i) {
-                if (k >= a && k < b && i == k_p) break;
-                if (i > 0) m &= ~(1ull << (i - 1));
-                m |= 1ull << i;
-                if (m < a) m |= 1ull << (i + 1);
-                const uint64_t m_i = hrr_refine(m, i + 1, a, b);
-                if (m_i >= a && m_i < b) k = m_i;
-            }
-        }
-        if (!(k >= a && k < b) || (r != 0u && __brev((uint32_t)k) < T)) k = hrr_alg1(a, b);
-    }
-    *argmin = (uint32_t)k;
-    return __brev((uint32_t)k) + r;
-}
-
 // Exact per-pair test (round to nearest, canonical order, no FMA): accept iff
 // xi < ceil(p 2^32), p = min(1, (tau I) / max(d2, 1e-4)). For 0 < p < 1, p 2^32 is an
 // exact float below 2^32, so its ceiling fits in 32 bits.

@@ -1,4 +1,4 @@
-// Batched range minimum of the shifted base-2 radical inverse (Sec. 2, Alg. 1-3).
+// Batched range minimum of the shifted base-2 radical inverse (Sec. 2).
 //
 // One query reads (a, b, r) and writes the minimum and its index: 12 + 8 bytes that are
 // touched once, so the kernel is a streaming pass bounded by HBM bandwidth. Threads take
@@ -19,7 +19,7 @@ __device__ __forceinline__ uint32_t one_query(uint32_t a, uint32_t b, uint32_t r
         *k = hrr_range_argmin_select(a, b, __brev(0u - r));
         return __brev(*k) + r;
     }
-    return VARIANT == 1 ? hrr_rangemin_alg2(a, b, r, k) : hrr_rangemin_closed(a, b, r, k);
+    return hrr_rangemin_closed(a, b, r, k);
 }
 
 template <int VARIANT, bool ARGMIN>
@@ -98,6 +98,5 @@ int launch(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r
 int hrr_range_min_impl(hrr_ctx *ctx, const uint32_t *a, const uint32_t *b, const uint32_t *r,
                        uint32_t *out_min, uint32_t *out_argmin, uint64_t n, int variant) {
     if (variant == 0) return launch<0>(ctx, a, b, r, out_min, out_argmin, n);
-    if (variant == 1) return launch<1>(ctx, a, b, r, out_min, out_argmin, n);
     return launch<2>(ctx, a, b, r, out_min, out_argmin, n);
 }

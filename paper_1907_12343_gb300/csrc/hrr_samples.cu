@@ -77,7 +77,7 @@ __device__ __forceinline__ void flush(const SampleLaunch &P, const uint2 *wbuf, 
         base = __shfl_sync(0xFFFFFFFFu, base, leader);
         if (has) {
             const unsigned long long o = base + rank;
-            if (o < P.cap) P.pairs[(size_t)s * P.cap + o] = wbuf[k];
+            if (o < P.cap) __stcs(&P.pairs[(size_t)s * P.cap + o], wbuf[k]);  // streaming: written once
         }
     }
     __syncwarp();

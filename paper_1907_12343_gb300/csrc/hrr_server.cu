@@ -41,6 +41,7 @@ struct Job {
     hrr_job desc{};
     const uint32_t *tile = nullptr;
     uint32_t tile_w = 0, tile_h = 0;
+    hrr_tile_buf *ctx_tile = nullptr;  // the submitting context's tile, when the job reads it
     int slot = -1;
     uint2 *pairs = nullptr;
     uint64_t bytes = 0;
@@ -343,6 +344,7 @@ void destroy_resources(hrr_server *s) {
         Job *j = kv.second;
         if (j->pairs) cudaFreeAsync(j->pairs, s->stream);
         if (j->done_ev) cudaEventDestroy(j->done_ev);
+        hrr_tile_release(j->ctx_tile, s->stream);  // every job is done: nothing reads it any more
         delete j;
     }
     for (int k = 0; k < kRing; ++k)
@@ -452,10 +454,12 @@ int hrr_server_submit(hrr_server *s, hrr_ctx *ctx, const hrr_job *job, uint64_t 
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job refit lights are partly NULL");
     const uint32_t *tile = d.dev_tile;
     uint32_t tw = d.tile_w, th = d.tile_h;
+    hrr_tile_buf *ctx_tile = nullptr;
     if (!tile) {
         if (!ctx || !ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "job has no tile and no context tile is set");
         tile = hrr_tile_layer(ctx->tile, ctx->tile_w, ctx->tile_h, ctx->tile_d, d.sample_index);
         tw = ctx->tile_w; th = ctx->tile_h;
+        ctx_tile = ctx->tile_buf;
     } else if (tw == 0 || th == 0 || tw > 65536 || th > 65536 || d.tile_d > 65536) {
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job tile size is invalid");
     } else {
@@ -465,6 +469,8 @@ int hrr_server_submit(hrr_server *s, hrr_ctx *ctx, const hrr_job *job, uint64_t 
     if (!j) return hrr_fail(ctx, HRR_ERR_OOM, "host allocation of a job");
     j->desc = d;
     j->tile = tile; j->tile_w = tw; j->tile_h = th;
+    j->ctx_tile = ctx_tile;
+    hrr_tile_retain(ctx_tile);  // released with the job, so a new context tile cannot free it
     j->bytes = d.cap * sizeof(uint2);
     j->t_submit = Clock::now();
     {
@@ -477,6 +483,7 @@ int hrr_server_submit(hrr_server *s, hrr_ctx *ctx, const hrr_job *job, uint64_t 
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) {
         cudaEventDestroy(j->done_ev);
+        hrr_tile_release(j->ctx_tile, s->stream);
         delete j;
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "server is shutting down");
     }
@@ -534,6 +541,7 @@ int hrr_server_release(hrr_server *s, uint64_t ticket) {
     if (j->pairs) cudaFreeAsync(j->pairs, s->stream);
     if (j->admitted) s->used -= j->bytes;
     if (j->done_ev) cudaEventDestroy(j->done_ev);
+    hrr_tile_release(j->ctx_tile, s->stream);  // the job is done: its slices no longer read the tile
     s->jobs.erase(it);
     delete j;
     s->cv_work.notify_one();

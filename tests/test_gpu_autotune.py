@@ -30,7 +30,7 @@ def test_autotune_returns_a_candidate_and_all_tunings_agree(tmp_path):
     n = g["ex"].numel()
     ref = None
     for t in [None, Autotuner.launch_fields(best), {"rangemin_variant": 2, "blocks_per_sm": 2},
-              {"rangemin_variant": 0, "blocks_per_sm": 1}, {"rangemin_variant": 1, "blocks_per_sm": 3}]:
+              {"rangemin_variant": 0, "blocks_per_sm": 1}, {"rangemin_variant": 2, "blocks_per_sm": 3}]:
         pairs = torch.empty((256 * n, 2), dtype=torch.int32, device=dev())
         vis = torch.zeros(n, dtype=torch.int32, device=dev())
         st, cnt = ctx.cull(g["ex"], g["ey"], g["ez"], g["px"], g["py"], tree, tau, pairs, eye_visits=vis,

@@ -163,3 +163,41 @@ def test_more_frames_than_one_launch_holds(ctx):
     b.destroy()
     for _, _, tree, _ in up:
         tree.free()
+
+
+def test_new_context_tile_leaves_batch_and_job_on_their_tile(ctx):
+    # A batch (recorded graph) and a served job that read the context's tile keep reading
+    # the tile they were created with after hrr_set_shift_tile replaces it: the old tile
+    # stays alive (reference-counted) until the batch is destroyed and the job released.
+    import torch
+    import paper_1907_12343_gb300 as hrr
+    s = _scenes()[2]
+    fr = _frame(ctx, s, cap=256 * len(s["eye_pos"]))
+    fr.pop("tile")  # the frame reads the context tile
+    ctx.set_shift_tile(s["tile"])
+    pst, ref, ref_vis = _plain(ctx, fr)
+    assert pst == hrr.HRR_OK
+    b = hrr.Batch(ctx, [fr], use_graph=True)
+    srv = hrr.Server(ctx, 1 << 30, max_jobs=4)
+    other = (np.asarray(s["tile"], np.uint32) ^ np.uint32(0x5A5A5A5A)).astype(np.uint32)
+    t = srv.submit(fr["x"], fr["y"], fr["z"], fr["px"], fr["py"], fr["tree"], fr["tau"], len(ref) + 1024)
+    ctx.set_shift_tile(other)   # replaces (and would have freed) the tile both still use
+    torch.cuda.synchronize()
+    for _ in range(2):
+        b.launch()
+        st, counts, _ = b.results()
+        assert st == hrr.HRR_OK
+        got = fr["pairs"][:counts[0]].cpu().numpy().view(np.uint32)
+        assert np.array_equal(sorted_pairs(got), sorted_pairs(ref))
+    r = srv.wait(t, 60.0)
+    assert r["status"] == hrr.HRR_OK and r["count"] == len(ref)
+    host = srv.pairs(t, r)
+    assert np.array_equal(sorted_pairs(host), sorted_pairs(ref))
+    srv.release(t)
+    srv.destroy()
+    b.destroy()
+    # the context now culls with the new tile: a different set
+    st2, cnt2, pairs2, _ = run_cull(ctx, fr["_g"], fr["tree"], fr["tau"])
+    assert st2 == hrr.HRR_OK
+    assert not np.array_equal(sorted_pairs(pairs2), sorted_pairs(ref))
+    fr["tree"].free()

@@ -31,7 +31,7 @@ def _gpu(ctx, s, **kw):
     return res
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 2])
 def test_uniform_tiny_scene_equals_flat(ctx, variant):
     # 1024 eyes x 4096 lights, 32x32 tile, tau for ~32 accepted per eye
     s = synth.scene_uniform()
