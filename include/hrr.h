@@ -108,19 +108,36 @@ typedef struct hrr_cull_opts {
     /* added (mod 2^32) to every eye's shift: the sample offset psi(n) of the adaptive
      * sampling variant (Sec. 3), absorbed into the shift; 0 for the plain method */
     uint32_t shift_offset;
-    /* launch shape (results do not depend on it): resident 256-thread blocks per SM of the
+    /* launch shape (results do not depend on it): resident blocks per SM of the
      * persistent grid, 0 = as many as fit (at most 64); see hrr_autotune */
     uint32_t blocks_per_sm;
     /* sample index n: selects layer n mod d of a space-time tile (hrr_set_shift_tile_3d);
      * 0 for a plain tile */
     uint32_t sample_index;
+    /* traversal form (results do not depend on it; 0 = the library default for each):
+     *   node_width: 2 = binary records (a visit tests both children), 4 = the hierarchy read
+     *     with nodes of width four (a visit tests the four grandchildren);
+     *   ring_entries: stack entries per warp kept in shared memory, 128 or 256 for width 2,
+     *     256 or 512 for width 4;
+     *   threads_per_block: 128 or 256 (one eye per warp). */
+    uint32_t node_width;
+    uint32_t ring_entries;
+    uint32_t threads_per_block;
 } hrr_cull_opts;
 
-/* Launch parameters of the traversal (see hrr_cull_opts); none changes any result. */
+/* Launch parameters of the traversal (see hrr_cull_opts); none changes any result. Zero
+ * fields take the library defaults. */
 typedef struct hrr_tuning {
     int rangemin_variant;
     uint32_t blocks_per_sm;
+    uint32_t node_width;
+    uint32_t ring_entries;
+    uint32_t threads_per_block;
 } hrr_tuning;
+
+/* The tuning the library uses for zero fields (rangemin_variant 0, blocks_per_sm 0 = as many
+ * as fit, and the default node width, ring size and threads per block). */
+int hrr_default_tuning(hrr_tuning *out);
 
 /* ---- context --------------------------------------------------------------------------- */
 
@@ -420,11 +437,20 @@ int hrr_server_destroy(hrr_server *server);
 
 /* ---- autotuning ---------------------------------------------------------------------- */
 
-/* Time every candidate launch shape (range-minimum variants 0 and 2; 4, 5 or 6 resident
- * blocks per SM, capped by what fits) on the given eyes (a sample of a workload's size class)
- * and return the fastest in *best (its median time in *best_ms, may be NULL). dev_pairs /
- * cap as in hrr_cull and large enough for the sample. Results of every candidate are
- * identical; only the time differs. Synchronous. */
+/* Time every compiled form of the traversal on the given eyes (a sample of a workload's
+ * size class): range-minimum variants 0 and 2, node widths 2 and 4, both ring sizes of
+ * each width, 128 and 256 threads per block, each at the most resident blocks per SM that
+ * fit and at one block fewer. Fills tried[k] and tried_ms[k] (median of three timed runs
+ * after a warm-up) for k < *n_tried, in a fixed order. capacity is the length of both
+ * arrays; if it is too small (or an array is NULL) nothing is timed, *n_tried receives the
+ * number needed and the call returns HRR_ERR_INVALID_ARG. dev_pairs / cap as in hrr_cull
+ * and large enough for the sample. Results of every candidate are identical; only the time
+ * differs. Synchronous. */
+int hrr_autotune_all(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
+                     uint32_t *dev_pairs, uint64_t cap, hrr_tuning *tried, double *tried_ms,
+                     uint32_t capacity, uint32_t *n_tried);
+/* hrr_autotune_all, keeping the fastest candidate in *best (its median time in *best_ms,
+ * may be NULL). */
 int hrr_autotune(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tree, float tau,
                  uint32_t *dev_pairs, uint64_t cap, hrr_tuning *best, double *best_ms);
 

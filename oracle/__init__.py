@@ -112,6 +112,8 @@ def configure(L):
     for nm in ("or_cull_flat", "or_cull_hier"):
         getattr(L, nm).restype = C.POINTER(_Result)
         getattr(L, nm).argtypes = [C.POINTER(_Tree), P, P, P, P, u32, P, u32, u32, f32, i32]
+    L.or_cull_hier_w.restype = C.POINTER(_Result)
+    L.or_cull_hier_w.argtypes = [C.POINTER(_Tree), P, P, P, P, u32, P, u32, u32, f32, i32, i32]
     L.or_cull_free.restype = None
     L.or_cull_free.argtypes = [C.POINTER(_Result)]
     L.or_max_threads.restype = i32
@@ -295,7 +297,7 @@ def spacetime_layer(tile, sample_index: int = 0) -> np.ndarray:
     return tile
 
 
-def _cull(fn, tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, sample_index=0):
+def _cull(fn, tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, sample_index=0, width=None):
     eye_pos = np.ascontiguousarray(eye_pos, dtype=np.float32).reshape(-1, 3)
     px = np.ascontiguousarray(px, dtype=np.uint16)
     py = np.ascontiguousarray(py, dtype=np.uint16)
@@ -303,8 +305,9 @@ def _cull(fn, tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, 
     h, w = tile.shape
     ids = None if eye_ids is None else np.ascontiguousarray(eye_ids, dtype=np.uint32)
     n_e = len(eye_pos)
+    extra = () if width is None else (int(width),)
     res = fn(tree._t, _ptr(eye_pos), _ptr(px), _ptr(py), _ptr(ids) if ids is not None else None,
-             n_e, _ptr(tile), w, h, np.float32(tau), nthreads)
+             n_e, _ptr(tile), w, h, np.float32(tau), *extra, nthreads)
     try:
         r = res.contents
         n = int(r.n_pairs)
@@ -330,9 +333,14 @@ def cull_flat(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, 
     return _cull(lib().or_cull_flat, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads, sample_index)
 
 
-def cull_hier(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, sample_index=0):
-    """Hierarchical traversal with per-eye visit counts; must equal ``cull_flat``."""
-    return _cull(lib().or_cull_hier, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads, sample_index)
+def cull_hier(tree: Tree, eye_pos, px, py, tile, tau, eye_ids=None, nthreads=0, sample_index=0, width=2):
+    """Hierarchical traversal with per-eye visit counts; must equal ``cull_flat``. width 2
+    visits binary nodes; width 4 visits the tree as nodes of width four (even depths,
+    grandchildren tested), with visits counted per such node."""
+    if width not in (2, 4):
+        raise ValueError("width must be 2 or 4")
+    return _cull(lib().or_cull_hier_w, tree, eye_pos, px, py, tile, tau, eye_ids, nthreads, sample_index,
+                 width=width)
 
 
 def max_threads() -> int:

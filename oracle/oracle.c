@@ -767,15 +767,38 @@ or_cull_result *or_cull_flat(const or_tree *t, const float *eye_pos, const uint1
     return res;
 }
 
-/* Hierarchical Russian roulette (Sec. 1): top-down traversal from the root; at each
- * visited internal node both children are tested. A leaf child is accepted by the exact
- * pair test; an internal child with range [a,b) is pushed unless the minimum of the
- * shifted sequence over [a,b) passes the conservative cull test (or_node_culls), in which
- * case no light below it can be accepted. The root is always visited. */
-or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint16_t *px,
-                             const uint16_t *py, const uint32_t *eye_ids, uint32_t n_eyes,
-                             const uint32_t *tile, uint32_t w, uint32_t h, float tau,
-                             int nthreads)
+/* One child of a visited node during the hierarchical traversal: the leaf range [f, l]
+ * (inclusive) of that child and, if it is internal, its node number k. A leaf (f == l) is
+ * accepted by the exact pair test; an internal child is pushed unless the minimum of the
+ * eye's shifted sequence over [f, l] passes the conservative cull test (or_node_culls),
+ * in which case no light below it can be accepted. */
+static void consider_child(const or_tree *t, uint32_t f, uint32_t l, uint32_t k, uint32_t r, float tau,
+                           const float *e, id_list *acc, uint32_t *stack, int *sp)
+{
+    if (f == l) {
+        uint32_t xi = or_brev(f, 32) + r;
+        if ((uint64_t)xi < or_leaf_threshold(tau, &t->pos[3 * (uint64_t)f], t->inten[f], e))
+            list_push(acc, f);
+        return;
+    }
+    uint64_t arg;
+    uint32_t v = or_rangemin_trie(f, (uint64_t)l + 1, r, 32, &arg);
+    if (!or_node_culls(tau, &t->lo[3 * (uint64_t)k], &t->hi[3 * (uint64_t)k], t->imax[k], e, v))
+        stack[(*sp)++] = k;
+}
+
+/* Hierarchical Russian roulette (Sec. 1): top-down traversal from the root. With width 2
+ * each visited internal node tests its two children. With width 4 the binary tree is read
+ * as a tree of nodes of width four: a visited node tests its grandchildren (and any child
+ * that is a leaf), never its internal children, and only even-depth nodes are visited.
+ * Both give the flat set: the cull test is monotone (a smaller box, a smaller maximum
+ * intensity and a range minimum over a sub-range never turn a cull into a visit), so a
+ * grandchild whose parent would have been culled is culled too. The root is always
+ * visited; visits are counted per visited node of the traversal's width. */
+or_cull_result *or_cull_hier_w(const or_tree *t, const float *eye_pos, const uint16_t *px,
+                               const uint16_t *py, const uint32_t *eye_ids, uint32_t n_eyes,
+                               const uint32_t *tile, uint32_t w, uint32_t h, float tau, int width,
+                               int nthreads)
 {
     int nt = pick_threads(nthreads);
     (void)nt;
@@ -794,7 +817,9 @@ or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint1
                 list_push(&lists[j], 0);
             continue;
         }
-        uint32_t stack[256]; /* depth-first: at most one pending node per level, height <= 144 */
+        /* depth-first: at most 3 pending nodes per level (width 4; 1 for width 2) plus the
+         * last visit's pushes, height <= 144 */
+        uint32_t stack[256];
         int sp = 0;
         stack[sp++] = 0;
         uint64_t v_count = 0;
@@ -802,22 +827,16 @@ or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint1
             uint32_t node = stack[--sp];
             ++v_count;
             uint32_t s = t->split[node];
-            uint32_t child[2] = {s, s + 1};
             uint32_t cf[2] = {t->first[node], s + 1};
             uint32_t cl[2] = {s, t->last[node]};
+            uint32_t ck[2] = {s, s + 1};
             for (int c = 0; c < 2; ++c) {
-                if (cf[c] == cl[c]) {
-                    uint32_t i = cf[c];
-                    uint32_t xi = or_brev(i, 32) + r;
-                    if ((uint64_t)xi < or_leaf_threshold(tau, &t->pos[3 * (uint64_t)i], t->inten[i], e))
-                        list_push(&lists[j], i);
-                } else {
-                    uint32_t k = child[c];
-                    uint64_t arg;
-                    uint32_t v = or_rangemin_trie(cf[c], (uint64_t)cl[c] + 1, r, 32, &arg);
-                    if (!or_node_culls(tau, &t->lo[3 * (uint64_t)k], &t->hi[3 * (uint64_t)k],
-                                       t->imax[k], e, v))
-                        stack[sp++] = k;
+                if (width == 2 || cf[c] == cl[c]) {
+                    consider_child(t, cf[c], cl[c], ck[c], r, tau, e, &lists[j], stack, &sp);
+                } else { /* an internal child: test its two children instead */
+                    uint32_t s2 = t->split[ck[c]];
+                    consider_child(t, cf[c], s2, s2, r, tau, e, &lists[j], stack, &sp);
+                    consider_child(t, s2 + 1, cl[c], s2 + 1, r, tau, e, &lists[j], stack, &sp);
                 }
             }
         }
@@ -842,6 +861,14 @@ or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint1
     res->seconds = t1 - t0;
     res->threads = nt;
     return res;
+}
+
+or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint16_t *px,
+                             const uint16_t *py, const uint32_t *eye_ids, uint32_t n_eyes,
+                             const uint32_t *tile, uint32_t w, uint32_t h, float tau,
+                             int nthreads)
+{
+    return or_cull_hier_w(t, eye_pos, px, py, eye_ids, n_eyes, tile, w, h, tau, 2, nthreads);
 }
 
 void or_cull_free(or_cull_result *res)

@@ -102,6 +102,14 @@ or_cull_result *or_cull_hier(const or_tree *t, const float *eye_pos, const uint1
                              const uint16_t *py, const uint32_t *eye_ids, uint32_t n_eyes,
                              const uint32_t *tile, uint32_t w, uint32_t h, float tau,
                              int nthreads);
+/* The same traversal over the tree read with nodes of width 2 (each visit tests two
+ * children, as or_cull_hier) or 4 (each visit tests the grandchildren, and leaf children;
+ * only even-depth nodes are visited): the same accepted set, visits counted per node of
+ * that width. */
+or_cull_result *or_cull_hier_w(const or_tree *t, const float *eye_pos, const uint16_t *px,
+                               const uint16_t *py, const uint32_t *eye_ids, uint32_t n_eyes,
+                               const uint32_t *tile, uint32_t w, uint32_t h, float tau, int width,
+                               int nthreads);
 void or_cull_free(or_cull_result *res);
 
 int or_max_threads(void);

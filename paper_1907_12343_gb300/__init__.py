@@ -87,7 +87,8 @@ class hrr_server_info(C.Structure):
 class hrr_cull_opts(C.Structure):
     _fields_ = [("eye_visits", C.c_void_p), ("rangemin_variant", C.c_int),
                 ("shift_offset", C.c_uint32), ("blocks_per_sm", C.c_uint32),
-                ("sample_index", C.c_uint32)]
+                ("sample_index", C.c_uint32), ("node_width", C.c_uint32),
+                ("ring_entries", C.c_uint32), ("threads_per_block", C.c_uint32)]
 
 
 class hrr_peaks(C.Structure):
@@ -102,17 +103,29 @@ HRR_TOPOLOGY_RADIX, HRR_TOPOLOGY_COST = 0, 1
 TOPOLOGIES = {"radix": HRR_TOPOLOGY_RADIX, "cost": HRR_TOPOLOGY_COST}
 
 
+TUNING_FIELDS = ("rangemin_variant", "blocks_per_sm", "node_width", "ring_entries", "threads_per_block")
+
+
 class hrr_tuning(C.Structure):
-    _fields_ = [("rangemin_variant", C.c_int), ("blocks_per_sm", C.c_uint32)]
+    _fields_ = [("rangemin_variant", C.c_int), ("blocks_per_sm", C.c_uint32), ("node_width", C.c_uint32),
+                ("ring_entries", C.c_uint32), ("threads_per_block", C.c_uint32)]
 
     @classmethod
     def from_dict(cls, d):
         if d is None:
             return None
-        return cls(int(d.get("rangemin_variant", 0)), int(d.get("blocks_per_sm", 0)))
+        return cls(*(int(d.get(k, 0)) for k in TUNING_FIELDS))
 
     def to_dict(self):
-        return {"rangemin_variant": int(self.rangemin_variant), "blocks_per_sm": int(self.blocks_per_sm)}
+        return {k: int(getattr(self, k)) for k in TUNING_FIELDS}
+
+
+def _opts(eye_visits, tuning, rangemin_variant, shift_offset, sample_index):
+    """hrr_cull_opts from a tuning dict (its fields win) and the call's own arguments."""
+    t = tuning or {}
+    return hrr_cull_opts(_ptr(eye_visits), int(t.get("rangemin_variant", rangemin_variant)), int(shift_offset),
+                         int(t.get("blocks_per_sm", 0)), int(sample_index), int(t.get("node_width", 0)),
+                         int(t.get("ring_entries", 0)), int(t.get("threads_per_block", 0)))
 
 
 _P = C.c_void_p
@@ -156,6 +169,9 @@ _SIGS = {
     "hrr_server_create": (_i32, [_P, _u64, _u32, _u32, C.POINTER(hrr_tuning), C.POINTER(_P)]),
     "hrr_autotune": (_i32, [_P, hrr_eyes, _u32, _P, _f32, _P, _u64, C.POINTER(hrr_tuning),
                             C.POINTER(C.c_double)]),
+    "hrr_default_tuning": (_i32, [C.POINTER(hrr_tuning)]),
+    "hrr_autotune_all": (_i32, [_P, hrr_eyes, _u32, _P, _f32, _P, _u64, C.POINTER(hrr_tuning),
+                                C.POINTER(C.c_double), _u32, C.POINTER(_u32)]),
     "hrr_server_submit": (_i32, [_P, _P, C.POINTER(hrr_job), C.POINTER(_u64)]),
     "hrr_server_poll": (_i32, [_P, _u64, C.POINTER(hrr_job_result)]),
     "hrr_server_wait": (_i32, [_P, _u64, C.c_double, C.POINTER(hrr_job_result)]),
@@ -172,6 +188,13 @@ for _name, (_res, _args) in _SIGS.items():
     globals()[_name] = _f
 
 EXPORTED = tuple(_SIGS)
+
+
+def default_tuning() -> dict:
+    """The tuning the library uses for zero fields (hrr_default_tuning)."""
+    t = hrr_tuning()
+    hrr_default_tuning(C.byref(t))
+    return t.to_dict()
 
 
 class HRRError(RuntimeError):
@@ -286,9 +309,7 @@ class Context:
         E = hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py))
         cap = int(pairs.shape[0]) if pairs is not None else 0
         cnt = _u64()
-        t = tuning or {}
-        opts = hrr_cull_opts(_ptr(eye_visits), int(t.get("rangemin_variant", rangemin_variant)),
-                             shift_offset, int(t.get("blocks_per_sm", 0)), int(sample_index))
+        opts = _opts(eye_visits, tuning, rangemin_variant, shift_offset, sample_index)
         st = hrr_cull_ex(self.handle, E, n, tree.handle, float(tau), C.byref(opts),
                          _ptr(pairs) if cap else None, cap, C.byref(cnt))
         if st not in (HRR_OK, HRR_ERR_OVERFLOW):
@@ -304,9 +325,7 @@ class Context:
         E = hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py))
         cap = int(pairs.shape[0]) if pairs is not None else 0
         cnt = _u64()
-        t = tuning or {}
-        opts = hrr_cull_opts(None, int(t.get("rangemin_variant", rangemin_variant)), shift_offset,
-                             int(t.get("blocks_per_sm", 0)), int(sample_index))
+        opts = _opts(None, tuning, rangemin_variant, shift_offset, sample_index)
         st = hrr_cull_host(self.handle, E, n, tree.handle, float(tau), C.byref(opts),
                            _ptr(pairs) if cap else None, cap, C.byref(cnt))
         if st not in (HRR_OK, HRR_ERR_OVERFLOW):
@@ -353,6 +372,20 @@ class Context:
                                 int(pairs.shape[0]), C.byref(best), C.byref(ms)))
         return best.to_dict(), float(ms.value)
 
+    def autotune_all(self, x, y, z, px, py, tree: "Tree", tau: float, pairs):
+        """Every candidate tuning with its median time on these eyes: [(tuning dict, ms)]."""
+        E = hrr_eyes(_ptr(x), _ptr(y), _ptr(z), _ptr(px), _ptr(py))
+        need = _u32()
+        hrr_autotune_all(self.handle, E, int(x.numel()), tree.handle, float(tau), _ptr(pairs),
+                         int(pairs.shape[0]), None, None, 0, C.byref(need))
+        n = int(need.value)
+        tried = (hrr_tuning * n)()
+        ms = (C.c_double * n)()
+        got = _u32()
+        self.check(hrr_autotune_all(self.handle, E, int(x.numel()), tree.handle, float(tau), _ptr(pairs),
+                                    int(pairs.shape[0]), tried, ms, n, C.byref(got)))
+        return [(tried[k].to_dict(), float(ms[k])) for k in range(int(got.value))]
+
     def range_min(self, a, b, r, out_min, out_argmin=None, variant: int = 0):
         self.check(hrr_range_min(self.handle, _ptr(a), _ptr(b), _ptr(r), _ptr(out_min),
                                  _ptr(out_argmin), int(a.numel()), variant))
@@ -396,7 +429,7 @@ class Batch:
                 _ptr(fr["pairs"]) if fr["pairs"].shape[0] else None, int(fr["pairs"].shape[0]),
                 _ptr(fr.get("eye_visits")), d, int(fr.get("sample_index", 0)))
         h = _P()
-        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0)
+        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0, 0, 0, 0)
         ctx.check(hrr_batch_create(ctx.handle, arr, self.n, C.byref(tn), 1 if use_graph else 0,
                                    C.byref(h)))
         self.handle = h
@@ -436,7 +469,7 @@ class Server:
                  max_jobs: int = 1024, rangemin_variant: int = 0, tuning=None):
         self.ctx = ctx
         h = _P()
-        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0)
+        tn = hrr_tuning.from_dict(tuning) or hrr_tuning(rangemin_variant, 0, 0, 0, 0)
         ctx.check(hrr_server_create(ctx.handle, int(hbm_budget_bytes), int(slice_eyes), int(max_jobs),
                                     C.byref(tn), C.byref(h)))
         self.handle = h

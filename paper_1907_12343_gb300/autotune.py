@@ -1,7 +1,8 @@
-"""Per-size-class autotuning of the traversal's launch shape, cached in JSON.
+"""Per-size-class autotuning of the traversal's form and launch shape, cached in JSON.
 
-The traversal gives identical results for every launch shape (range-minimum variant,
-resident blocks per SM); only its speed depends on the workload.
+The traversal gives identical results for every tuning (range-minimum variant, node
+width, shared-memory stack ring, threads per block, resident blocks per SM); only its
+speed depends on the workload.
 ``Autotuner`` keys workloads by size class (bit lengths of N_l and N_e), tunes a class
 once on a sample of its eyes with ``hrr_autotune`` and stores the answer, so later
 frames, batches and servers of that class reuse it.
@@ -23,6 +24,7 @@ class Autotuner:
         self.path = cache_path
         self.sample = sample_eyes
         self.table: dict[str, dict] = {}
+        self.last_table: list = []  # every candidate's (tuning, ms) of the last tuning run
         if cache_path and os.path.exists(cache_path):
             with open(cache_path) as f:
                 self.table = json.load(f)
@@ -51,11 +53,15 @@ class Autotuner:
         import torch
         k = min(n_eyes, self.sample)
         pairs = torch.empty((max(k * 256, 1024), 2), dtype=torch.int32, device=x.device)
-        tuning, ms = self.ctx.autotune(x[:k], y[:k], z[:k], px[:k], py[:k], tree, tau, pairs)
-        return self.put(n_eyes, n_lights, tuning, ms)
+        table = self.ctx.autotune_all(x[:k], y[:k], z[:k], px[:k], py[:k], tree, tau, pairs)
+        tuning, ms = min(table, key=lambda tm: tm[1])
+        entry = self.put(n_eyes, n_lights, tuning, ms)
+        self.last_table = table
+        return entry
 
     @staticmethod
     def launch_fields(entry: dict | None) -> dict | None:
         if entry is None:
             return None
-        return {k: entry[k] for k in ("rangemin_variant", "blocks_per_sm")}
+        from . import TUNING_FIELDS
+        return {k: entry[k] for k in TUNING_FIELDS if k in entry}

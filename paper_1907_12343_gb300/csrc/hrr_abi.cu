@@ -64,6 +64,12 @@ const char *hrr_status_string(int s) {
 
 const char *hrr_last_error(const hrr_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+int hrr_default_tuning(hrr_tuning *out) {
+    if (!out) return HRR_ERR_INVALID_ARG;
+    *out = hrr_tuning_normalized(hrr_tuning{});
+    return HRR_OK;
+}
+
 int hrr_create(hrr_ctx **out, int device, void *cuda_stream) {
     if (!out) return HRR_ERR_INVALID_ARG;
     *out = nullptr;
@@ -184,6 +190,7 @@ int hrr_free_light_tree(hrr_ctx *ctx, hrr_tree *tree) {
     DeviceGuard g(ctx->device);
     if (tree->nodes) HRR_CUDA(ctx, cudaFreeAsync(tree->nodes, ctx->stream));
     if (tree->perm) HRR_CUDA(ctx, cudaFreeAsync(tree->perm, ctx->stream));
+    if (tree->wide) HRR_CUDA(ctx, cudaFreeAsync(tree->wide, ctx->stream));
     delete tree;
     return HRR_OK;
 }
@@ -229,7 +236,7 @@ int hrr_refit_light_tree(hrr_ctx *ctx, hrr_tree *tree, hrr_lights lights) {
     void *scratch = nullptr;
     HRR_CUDA(ctx, cudaMallocAsync(&scratch, hrr_refit_scratch_bytes(tree->n), st));
     const cudaError_t e = hrr_refit_enqueue(tree, lights, scratch, flags, st);
-    ctx->launches += tree->n > 1 ? 3 : 1;
+    ctx->launches += tree->n > 1 ? 4 : 2;
     cudaFreeAsync(scratch, st);
     HRR_CUDA(ctx, e);
     HRR_CUDA(ctx, cudaMemcpyAsync(&ctx->host_counters[2], flags, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
@@ -290,8 +297,10 @@ int hrr_cull_ex(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const hrr_tree *tr
     if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
     hrr_cull_opts o{};
     if (opts) o = *opts;
-    if ((o.rangemin_variant != 0 && o.rangemin_variant != 2) || o.blocks_per_sm > 64)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0 or 2 and blocks_per_sm <= 64");
+    if (!hrr_tuning_valid(hrr_tuning_of(o)))
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG,
+                        "rangemin_variant must be 0 or 2, blocks_per_sm <= 64, node_width 2 or 4, "
+                        "threads_per_block 128 or 256, ring_entries 128/256 (width 2) or 256/512 (width 4)");
     DeviceGuard g(ctx->device);
     return hrr_cull_impl(ctx, eyes, n_eyes, tree, tau, o, dev_pairs, cap, out_count);
 }
@@ -336,8 +345,10 @@ int hrr_cull_host(hrr_ctx *ctx, hrr_eyes host_eyes, uint32_t n_eyes, const hrr_t
     if (!ctx->tile) return hrr_fail(ctx, HRR_ERR_NO_TILE, "no shift tile set");
     hrr_cull_opts o{};
     if (opts) o = *opts;
-    if ((o.rangemin_variant != 0 && o.rangemin_variant != 2) || o.blocks_per_sm > 64)
-        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "rangemin_variant must be 0 or 2 and blocks_per_sm <= 64");
+    if (!hrr_tuning_valid(hrr_tuning_of(o)))
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG,
+                        "rangemin_variant must be 0 or 2, blocks_per_sm <= 64, node_width 2 or 4, "
+                        "threads_per_block 128 or 256, ring_entries 128/256 (width 2) or 256/512 (width 4)");
     DeviceGuard g(ctx->device);
     return hrr_cull_host_impl(ctx, host_eyes, n_eyes, tree, tau, o, host_pairs, cap, out_count);
 }

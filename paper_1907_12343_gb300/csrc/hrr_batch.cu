@@ -118,7 +118,11 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
         hrr_cull_frame_t &d = b->desc[i];
         d = hrr_cull_frame_t{};
         d.ex = fr.eyes.x; d.ey = fr.eyes.y; d.ez = fr.eyes.z; d.px = fr.eyes.px; d.py = fr.eyes.py;
-        d.nodes = reinterpret_cast<const float4 *>(fr.tree->nodes);
+        d.nodes = hrr_cull_records(fr.tree, b->tuning);
+        if (!d.nodes) {
+            release(b);
+            return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "a frame's tree has no records of the tuning's node width");
+        }
         d.perm = fr.tree->perm;
         d.tile = fr.dev_tile ? hrr_tile_layer(fr.dev_tile, fr.tile_w, fr.tile_h, fr.tile_d, fr.sample_index)
                              : hrr_tile_layer(ctx->tile, ctx->tile_w, ctx->tile_h, ctx->tile_d, fr.sample_index);
@@ -144,8 +148,8 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
         pt.grid = hrr_cull_grid(ctx->sm_count, b->tuning, true, pt.total);
         grid_max = std::max(grid_max, pt.grid);
     }
-    b->spill_cap = hrr_cull_spill_cap(height);
-    cudaError_t e = cudaMalloc(&b->spill, hrr_cull_spill_entries(grid_max, height) * sizeof(uint2));
+    b->spill_cap = hrr_cull_spill_cap(height, b->tuning.node_width);
+    cudaError_t e = cudaMalloc(&b->spill, hrr_cull_spill_entries(grid_max, height, b->tuning) * sizeof(uint2));
     if (e == cudaSuccess) e = cudaMalloc(&b->dev_counts, sizeof(unsigned long long) * b->n_counters());
     if (e == cudaSuccess) e = cudaMallocHost(&b->host_counts, sizeof(unsigned long long) * b->n_counters());
     if (e != cudaSuccess) {

@@ -317,6 +317,64 @@ __global__ void single_leaf_kernel(const float *x, const float *y, const float *
     perm[0] = 0;
 }
 
+// Records of width four. The record of internal node g holds, in this order, the slots of
+// g's grandchildren over its leaf range [first, last] split at `split`:
+//   slot 0: [first, s0]      slot 1: [s0 + 1, split]     (the children of child 0)
+//   slot 2: [split + 1, s1]  slot 3: [s1 + 1, last]      (the children of child 1)
+// each 32 bytes: box low corner, maximum intensity, box high corner, and one index word
+// (s0, split, s1 and g's other range end, in slot order). A child that is a leaf takes its
+// first slot as itself (s0 = split, or s1 = last) and leaves the second slot empty (an
+// empty range). The internal slots are binary nodes s0, s0 + 1, s1, s1 + 1, whose own
+// records sit at those indices. Since a node's record is the first 32 bytes of its
+// children's binary records, re-labelled, the widening is a gather of the binary records.
+__global__ void __launch_bounds__(kThreads) widen_kernel(const float4 *__restrict__ nodes, uint32_t n,
+                                                         float4 *__restrict__ wide,
+                                                         const unsigned long long *flags) {
+    const uint32_t g = blockIdx.x * kThreads + threadIdx.x;
+    if (*(volatile const unsigned long long *)flags & HRR_FLAG_NONFINITE) return;
+    if (n == 1) {  // the single leaf in slot 0, the rest empty
+        if (g == 0) {
+            wide[0] = nodes[0];
+            wide[1] = nodes[1];
+            for (int k = 2; k < 8; ++k) wide[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        return;
+    }
+    if (g >= n - 1) return;
+    const float4 *r = nodes + 4 * (size_t)g;
+    const float4 c0l = r[0], c0h = r[1], c1l = r[2], c1h = r[3];
+    const uint32_t split = __float_as_uint(c0h.w), other = __float_as_uint(c1h.w);
+    const uint32_t first = min(g, other), last = max(g, other);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 *w = wide + 8 * (size_t)g;
+    if (first == split) {  // child 0 is a leaf: slot 0 is the leaf, slot 1 empty
+        w[0] = c0l;
+        w[1] = make_float4(c0h.x, c0h.y, c0h.z, __uint_as_float(split));
+        w[2] = zero;
+        w[3] = make_float4(0.f, 0.f, 0.f, __uint_as_float(split));
+    } else {  // the children of internal node `split`
+        const float4 *a = nodes + 4 * (size_t)split;
+        w[0] = a[0];
+        w[1] = a[1];  // its .w is the child's split, s0
+        w[2] = a[2];
+        const float4 h = a[3];
+        w[3] = make_float4(h.x, h.y, h.z, __uint_as_float(split));
+    }
+    if (split + 1u == last) {  // child 1 is a leaf
+        w[4] = c1l;
+        w[5] = make_float4(c1h.x, c1h.y, c1h.z, __uint_as_float(last));
+        w[6] = zero;
+        w[7] = make_float4(0.f, 0.f, 0.f, __uint_as_float(other));
+    } else {  // the children of internal node split + 1
+        const float4 *b = nodes + 4 * (size_t)(split + 1u);
+        w[4] = b[0];
+        w[5] = b[1];  // s1
+        w[6] = b[2];
+        const float4 h = b[3];
+        w[7] = make_float4(h.x, h.y, h.z, __uint_as_float(other));
+    }
+}
+
 template <typename T>
 T *carve(char *&p, size_t count) {
     T *r = reinterpret_cast<T *>(p);
@@ -909,12 +967,14 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
     auto fail = [&](int status) {
         if (tree->nodes) cudaFreeAsync(tree->nodes, st);
         if (tree->perm) cudaFreeAsync(tree->perm, st);
+        if (tree->wide) cudaFreeAsync(tree->wide, st);
         delete tree;
         return status;
     };
     const uint32_t n_rec = n > 1 ? n - 1 : 1;
     cudaError_t e = cudaMallocAsync(&tree->nodes, sizeof(hrr_node) * (size_t)n_rec, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&tree->perm, sizeof(uint32_t) * (size_t)n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&tree->wide, 8 * sizeof(float4) * (size_t)n_rec, st);
     if (e != cudaSuccess) return fail(hrr_cuda_fail(ctx, e, "tree allocation"));
     unsigned long long *flags = ctx->counters + 2;
     if ((e = cudaMemsetAsync(flags, 0, sizeof(unsigned long long), st)) != cudaSuccess)
@@ -985,6 +1045,8 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
         cudaFreeAsync(scratch, st);
         if (rc != HRR_OK) return fail(rc);
     }
+    if ((e = hrr_widen_enqueue(tree, flags, st)) != cudaSuccess) return fail(hrr_cuda_fail(ctx, e, "widen_kernel"));
+    ++ctx->launches;
     if ((e = cudaMemcpyAsync(&ctx->host_counters[2], flags, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return fail(hrr_cuda_fail(ctx, e, "flag copy"));
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(hrr_cuda_fail(ctx, e, "build"));
@@ -1014,7 +1076,8 @@ cudaError_t hrr_refit_enqueue(hrr_tree *tree, const hrr_lights &L, void *scratch
     if (n == 1) {
         // one leaf: rewrite the single record unless the light is not finite (checked there)
         single_leaf_kernel<<<1, 1, 0, st>>>(L.x, L.y, L.z, L.intensity, tree->nodes, tree->perm, flags);
-        return cudaGetLastError();
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? hrr_widen_enqueue(tree, flags, st) : e;
     }
     char *p = static_cast<char *>(scratch_mem);
     float4 *spos = carve<float4>(p, n);
@@ -1031,6 +1094,15 @@ cudaError_t hrr_refit_enqueue(hrr_tree *tree, const hrr_lights &L, void *scratch
     links_kernel<<<gi, kThreads, 0, st>>>(tree->nodes, n, leaf_parent, int_parent, flags);
     refit_kernel<<<g, kThreads, 0, st>>>(spos, n, tree->nodes, leaf_parent, int_parent, arrivals, child_height,
                                          root_height, flags);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? hrr_widen_enqueue(tree, flags, st) : e;
+}
+
+cudaError_t hrr_widen_enqueue(hrr_tree *tree, const unsigned long long *flags, cudaStream_t st) {
+    if (!tree->wide) return cudaSuccess;
+    const uint32_t n = tree->n;
+    const unsigned g = n > 1 ? (n - 1 + kThreads - 1) / kThreads : 1;
+    widen_kernel<<<g, kThreads, 0, st>>>(reinterpret_cast<const float4 *>(tree->nodes), n, tree->wide, flags);
     return cudaGetLastError();
 }
 

@@ -362,6 +362,10 @@ int hrr_build_scene(hrr_ctx *ctx, const float *dev_tris, uint32_t n_tris, hrr_sc
     int rc = hrr_build_impl(ctx, L, n_tris, &tree);  // the centroids' radix tree (synchronous)
     cudaFreeAsync(cen, st);
     if (rc != HRR_OK) return rc;
+    if (tree->wide) {  // the segment walk reads the binary records only
+        cudaFreeAsync(tree->wide, st);
+        tree->wide = nullptr;
+    }
     hrr_scene *sc = new (std::nothrow) hrr_scene();
     if (!sc) {
         hrr_free_light_tree(ctx, tree);

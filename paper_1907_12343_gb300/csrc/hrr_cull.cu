@@ -5,16 +5,34 @@
 #include "hrr_cull_kernel.cuh"
 
 unsigned hrr_cull_grid(int sm_count, const hrr_tuning &tuning, bool batch, unsigned long long total) {
-    int per_sm = batch ? occupancy_of<true>(tuning.rangemin_variant) : occupancy_of<false>(tuning.rangemin_variant);
+    CullKernel *k = cull_kernel_for(tuning);
+    if (!k) return 1;
+    int per_sm = cull_occupancy(*k, batch);
     if (tuning.blocks_per_sm > 0 && (int)tuning.blocks_per_sm < per_sm) per_sm = (int)tuning.blocks_per_sm;
-    const unsigned long long needed = (total + kWarps - 1) / kWarps;
+    const unsigned warps = (unsigned)k->threads / 32u;
+    const unsigned long long needed = (total + warps - 1) / warps;
     return (unsigned)std::max<unsigned long long>(1ull, std::min<unsigned long long>((unsigned long long)per_sm * sm_count, needed));
 }
 
-uint32_t hrr_cull_spill_cap(uint32_t height) { return 32u * (height + 2u) + 64u; }
+int hrr_cull_max_blocks(const hrr_tuning &tuning, bool batch) {
+    CullKernel *k = cull_kernel_for(tuning);
+    return k ? cull_occupancy(*k, batch) : 0;
+}
 
-size_t hrr_cull_spill_entries(unsigned grid, uint32_t height) {
-    return (size_t)grid * kWarps * hrr_cull_spill_cap(height);
+// The stack of a width-w traversal of a tree of height H holds at most (w - 1) 32 L + 32
+// entries, L the depth levels a pushed node can sit at (binary: H - 1; width four: the even
+// depths below the root, (H - 1) / 2); the spill writes stay below the stack size.
+uint32_t hrr_cull_spill_cap(uint32_t height, uint32_t width) {
+    const uint32_t levels = height == 0 ? 0u : (width == 4 ? (height - 1u) / 2u : height - 1u);
+    return (width - 1u) * 32u * levels + 32u + 64u;
+}
+
+size_t hrr_cull_spill_entries(unsigned grid, uint32_t height, const hrr_tuning &tuning) {
+    return (size_t)grid * (tuning.threads_per_block / 32u) * hrr_cull_spill_cap(height, tuning.node_width);
+}
+
+const float4 *hrr_cull_records(const hrr_tree *tree, const hrr_tuning &tuning) {
+    return tuning.node_width == 4 ? tree->wide : reinterpret_cast<const float4 *>(tree->nodes);
 }
 
 namespace {
@@ -36,10 +54,10 @@ int ensure_spill(hrr_ctx *ctx, size_t need) {
 
 // The single-frame descriptor of one culling launch over eyes [eye_begin, eye_begin + n).
 Frame single_frame(const hrr_ctx *ctx, const hrr_eyes &E, const hrr_tree *tree, float tau, const hrr_cull_opts &opts,
-                   uint32_t *pairs, uint64_t cap, uint32_t eye_begin) {
+                   const hrr_tuning &tn, uint32_t *pairs, uint64_t cap, uint32_t eye_begin) {
     Frame fr{};
     fr.ex = E.x; fr.ey = E.y; fr.ez = E.z; fr.px = E.px; fr.py = E.py;
-    fr.nodes = reinterpret_cast<const float4 *>(tree->nodes);
+    fr.nodes = hrr_cull_records(tree, tn);
     fr.perm = tree->perm;
     fr.tile = hrr_tile_layer(ctx->tile, ctx->tile_w, ctx->tile_h, ctx->tile_d, opts.sample_index);
     fr.pairs = reinterpret_cast<uint2 *>(pairs);
@@ -79,17 +97,20 @@ int hrr_cull_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, const hrr_tr
                   float tau, const hrr_cull_opts &opts, uint32_t *pairs, uint64_t cap,
                   uint64_t *out_count) {
     if (((uintptr_t)pairs & 7u) != 0) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "dev_pairs must be 8-byte aligned");
+    const hrr_tuning tn = hrr_tuning_of(opts);
+    CullKernel *kern = cull_kernel_for(tn);
+    if (!kern) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "no compiled traversal for these options");
+    if (!hrr_cull_records(tree, tn)) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "the tree has no records of this width");
     cudaStream_t st = ctx->stream;
     HRR_CUDA(ctx, cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), st));
     if (n_eyes > 0) {
-        const hrr_tuning tn = hrr_tuning_of(opts);
         const unsigned grid = hrr_cull_grid(ctx->sm_count, tn, false, n_eyes);
-        if (int rc = ensure_spill(ctx, hrr_cull_spill_entries(grid, tree->height))) return rc;
-        const Frame fr = single_frame(ctx, E, tree, tau, opts, pairs, cap, 0);
-        const Launch Lc{1, hrr_cull_spill_cap(tree->height), n_eyes, ctx->counters + 3, ctx->counters + 2,
-                        reinterpret_cast<uint2 *>(ctx->spill)};
+        if (int rc = ensure_spill(ctx, hrr_cull_spill_entries(grid, tree->height, tn))) return rc;
+        const Frame fr = single_frame(ctx, E, tree, tau, opts, tn, pairs, cap, 0);
+        const Launch Lc{1, hrr_cull_spill_cap(tree->height, tn.node_width), n_eyes, ctx->counters + 3,
+                        ctx->counters + 2, reinterpret_cast<uint2 *>(ctx->spill)};
         hrr_timing_begin(ctx);
-        const cudaError_t e = launch_single(tn, grid, Lc, fr, st);
+        const cudaError_t e = launch_single(*kern, grid, Lc, fr, st);
         hrr_timing_end(ctx);
         ++ctx->launches;
         HRR_CUDA(ctx, e);
@@ -157,10 +178,13 @@ int hrr_cull_host_impl(hrr_ctx *ctx, const hrr_eyes &H, uint32_t n_eyes, const h
     // slices of about 2^18 eyes or more
     const uint32_t slices = n_eyes == 0 ? 0u : std::max(1u, std::min<uint32_t>(HRR_HOST_SLICES, (n_eyes + (1u << 17)) >> 18));
     const hrr_tuning tn = hrr_tuning_of(opts);
+    CullKernel *kern = cull_kernel_for(tn);
+    if (!kern) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "no compiled traversal for these options");
+    if (!hrr_cull_records(tree, tn)) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "the tree has no records of this width");
     if (slices) {
         const unsigned grid = hrr_cull_grid(ctx->sm_count, tn, false, n_eyes);  // at least any slice's grid
         // two slices may run at once, each with its own spill area
-        if (int rc = ensure_spill(ctx, 2 * hrr_cull_spill_entries(grid, tree->height))) return rc;
+        if (int rc = ensure_spill(ctx, 2 * hrr_cull_spill_entries(grid, tree->height, tn))) return rc;
     }
     cudaStream_t cs[2] = {st, ctx->stream2};
     HRR_CUDA(ctx, cudaMemsetAsync(ctx->counters, 0, 4 * sizeof(unsigned long long), st));
@@ -202,11 +226,12 @@ int hrr_cull_host_impl(hrr_ctx *ctx, const hrr_eyes &H, uint32_t n_eyes, const h
         cudaError_t r = cudaStreamWaitEvent(s, ctx->ev_in[i], 0);
         if (r == cudaSuccess && i >= 2) r = cudaStreamWaitEvent(s, ctx->ev_out[i - 2], 0);  // buffer reuse
         if (r != cudaSuccess) return r;
-        Frame fr = single_frame(ctx, D, tree, tau, opts, buf[i & 1], cap, e0);
+        Frame fr = single_frame(ctx, D, tree, tau, opts, tn, buf[i & 1], cap, e0);
         fr.counts = cnt;
-        const Launch Lc{1, hrr_cull_spill_cap(tree->height), (unsigned long long)(e1 - e0), cnt + 3, ctx->counters + 2,
-                        reinterpret_cast<uint2 *>(ctx->spill) + (i & 1) * hrr_cull_spill_entries(grid_cap, tree->height)};
-        r = launch_single(tn, hrr_cull_grid(ctx->sm_count, tn, false, e1 - e0), Lc, fr, s);
+        const Launch Lc{1, hrr_cull_spill_cap(tree->height, tn.node_width), (unsigned long long)(e1 - e0), cnt + 3,
+                        ctx->counters + 2,
+                        reinterpret_cast<uint2 *>(ctx->spill) + (i & 1) * hrr_cull_spill_entries(grid_cap, tree->height, tn)};
+        r = launch_single(*kern, hrr_cull_grid(ctx->sm_count, tn, false, e1 - e0), Lc, fr, s);
         ++ctx->launches;
         if (r == cudaSuccess)
             r = cudaMemcpyAsync(&ctx->host_slices[4 * i], cnt, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
@@ -255,9 +280,11 @@ cudaError_t hrr_cull_batch_enqueue(unsigned grid, const hrr_cull_frame_t *frames
                                    const hrr_tuning &tuning, cudaStream_t st) {
     if (total == 0) return cudaSuccess;
     if (n_frames == 0 || n_frames > kMaxFrames) return cudaErrorInvalidValue;
+    CullKernel *kern = cull_kernel_for(hrr_tuning_normalized(tuning));
+    if (!kern) return cudaErrorInvalidValue;
     FrameArray<kMaxFrames> fa;
     for (uint32_t i = 0; i < n_frames; ++i) fa.f[i] = frames[i];
     for (uint32_t i = n_frames; i < kMaxFrames; ++i) fa.f[i] = Frame{};
     const Launch Lc{n_frames, spill_cap, total, cursor, flags, static_cast<uint2 *>(spill)};
-    return launch_batch(hrr_tuning_normalized(tuning), grid, Lc, fa, st);
+    return launch_batch(*kern, grid, Lc, fa, st);
 }

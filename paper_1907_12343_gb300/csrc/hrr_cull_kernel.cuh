@@ -3,12 +3,20 @@
 // Hierarchical Russian-roulette culling with blue-noise dithered QMC sequences (Sec. 1).
 //
 // For eye j with shift r_j (tile entry at its pixel), the traversal starts at the root and,
-// at every visited internal node, tests both children from the node's 64-byte record:
+// at every visited node, tests the node's children from one record:
 //   * a leaf child i is accepted iff brev(i) + r_j < ceil(p_ij 2^32) (exact float32 p);
 //   * an internal child with leaf range [a, b) is descended unless the range minimum
 //     v(a, b) = min_{i in [a,b)} (brev(i) + r_j) mod 2^32 passes the conservative cull test
 //     (v is at least the threshold of every light below; then none can be accepted).
 // The accepted set therefore equals flat Russian roulette over all pairs.
+//
+// Node width. The hierarchy is binary; a traversal reads it either with binary nodes
+// (64-byte records: both children) or with nodes of width four (128-byte records: the four
+// grandchildren, or a leaf child in place of its two slots), visiting only even-depth nodes.
+// The cull test is monotone (a smaller box, a smaller maximum intensity and a range minimum
+// over a sub-range never turn a cull into a visit), so both widths accept the same pairs;
+// width four pops half as many nodes, with half the stack traffic and loop overhead per
+// child tested, for one extra range minimum per visit.
 //
 // Execution: a persistent grid (a whole number of resident blocks per SM) in which each
 // warp traverses one eye at a time. The warp's stack of pending nodes is a ring in shared
@@ -16,49 +24,46 @@
 // that survive their tests back as one compacted run (ballot + popc). All lanes of a step
 // execute the same node test on the same eye, so the warp stays converged except at leaf
 // children. When the ring would overflow, its oldest entries move to a per-warp area in
-// global memory, and they come back when the ring runs low.
+// global memory, and they come back when the ring runs low. The stack never exceeds
+// (w - 1) * 32 * L + 32 entries for node width w and L depth levels of pushed nodes (each
+// remainder of a pushed run below the top holds at most (w - 1) * 32 entries, and the
+// shallowest depth of those runs grows from the bottom of the stack to its top), and the
+// spill area is sized by that bound.
 //
 // Memory: the kernel is bound by the L1 data pipe (one scattered record per lane per
-// step), so each record is fetched with two 256-bit loads instead of four 128-bit ones.
-// A node's range minimum is attained at its argmin, which lies in exactly one child;
-// carrying the argmin with each stack entry means only the other child's minimum has to be
-// computed. Accepted pairs are staged per warp in shared memory and appended to the output
-// with one atomic per frame and coalesced 8-byte stores.
+// step), so each record is fetched with 256-bit loads. A node's range minimum is attained at
+// its argmin, which lies in exactly one child; carrying the argmin with each stack entry
+// means only the other children's minima have to be computed. Accepted pairs are staged
+// per warp in shared memory and appended to the output with one atomic per frame and
+// coalesced 8-byte stores.
 //
 // One launch may cover many frames (a batch): the eye cursor then runs over the eyes of all
 // frames, each warp finds its eye's frame by binary search over the frames' cursor offsets,
-// and the frames' descriptors are staged in shared memory. Frames of different sizes share
-// the launch without any per-frame tail.
+// and the frames' descriptors are read through the constant cache. Frames of different
+// sizes share the launch without any per-frame tail.
 #pragma once
 
 #include <algorithm>
+#include <vector>
 
 #include "hrr_internal.cuh"
 
 namespace {
 
-// Launch shape, fixed at compile time (the values measured fastest on GB300).
-#ifndef HRR_CULL_MIN_BLOCKS
-#define HRR_CULL_MIN_BLOCKS 6  // resident 256-thread blocks per SM (40 registers, no spills)
-#endif
-#ifndef HRR_CULL_BATCH_MIN_BLOCKS
-#define HRR_CULL_BATCH_MIN_BLOCKS 6  // the batched form: frame fields come from the constant cache
-#endif
-#ifndef HRR_CULL_RING
-#define HRR_CULL_RING 256  // stack entries per warp kept in shared memory (a power of two)
-#endif
 #ifndef HRR_CULL_BUF
 #define HRR_CULL_BUF 128  // staged output pairs per warp
 #endif
 
-constexpr int kThreads = HRR_CULL_THREADS;
-constexpr int kWarps = kThreads / 32;
 constexpr int kBuf = HRR_CULL_BUF;
-constexpr uint32_t kRing = HRR_CULL_RING;
-constexpr uint32_t kRingMask = kRing - 1;
-static_assert((kRing & kRingMask) == 0 && kRing >= 128, "ring size");
 constexpr uint32_t kMaxFrames = HRR_CULL_MAX_FRAMES;  // frames of one batched launch
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// Resident threads per SM each instantiation is compiled for (the register budget):
+// 40 registers for binary records (6 blocks of 256 threads), 64 for width four.
+template <int W>
+constexpr int min_blocks(int threads) {
+    return (W == 2 ? 1536 : 1024) / threads;
+}
 
 using Frame = hrr_cull_frame_t;
 static_assert(sizeof(Frame) == 128, "frame descriptor layout");
@@ -86,14 +91,10 @@ __device__ __forceinline__ const Frame &frame_at(const Frame *F, uint32_t f) {
     else return F[f];
 }
 
-// The 64-byte node record (both children) as two 256-bit read-only loads.
-__device__ __forceinline__ void load_record(const float4 *p, float4 &q0, float4 &q1, float4 &q2,
-                                            float4 &q3) {
+// 32 bytes (two float4) as one 256-bit read-only load.
+__device__ __forceinline__ void load32(const float4 *p, float4 &a, float4 &b) {
     asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(q0.x), "=f"(q0.y), "=f"(q0.z), "=f"(q0.w), "=f"(q1.x), "=f"(q1.y), "=f"(q1.z), "=f"(q1.w)
-        : "l"(p));
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
-        : "=f"(q2.x), "=f"(q2.y), "=f"(q2.z), "=f"(q2.w), "=f"(q3.x), "=f"(q3.y), "=f"(q3.z), "=f"(q3.w)
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
         : "l"(p));
 }
 
@@ -134,29 +135,33 @@ __device__ __forceinline__ void flush(const Frame *F, const uint2 *wbuf, const u
     __syncwarp();
 }
 
-// Stage up to two accepted leaves per lane of eye j (warp-collective).
-template <bool BATCH>
+// Stage the accepted leaves (up to W per lane, kNone for none) of eye j (warp-collective).
+template <bool BATCH, int W>
 __device__ __forceinline__ void emit(const Frame *F, uint2 *wbuf, uint16_t *wfr, uint32_t &cnt, int lane,
-                                     uint32_t f, uint32_t j, uint32_t acc0, uint32_t acc1) {
-    const unsigned b0 = __ballot_sync(0xFFFFFFFFu, acc0 != kNone);
-    const unsigned b1 = __ballot_sync(0xFFFFFFFFu, acc1 != kNone);
-    const uint32_t tot = __popc(b0) + __popc(b1);
+                                     uint32_t f, uint32_t j, const uint32_t (&acc)[W]) {
+    unsigned bal[W];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        bal[k] = __ballot_sync(0xFFFFFFFFu, acc[k] != kNone);
+        tot += __popc(bal[k]);
+    }
     if (tot == 0) return;
-    if (cnt + tot > (uint32_t)kBuf) {
+    if (cnt + tot > (uint32_t)kBuf) {  // tot <= 32 W <= kBuf
         flush<BATCH>(F, wbuf, wfr, cnt, lane);
         cnt = 0;
     }
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t *perm = frame_at<BATCH>(F, f).perm;
-    if (acc0 != kNone) {
-        const uint32_t o = cnt + __popc(b0 & lt);
-        wbuf[o] = make_uint2(j, __ldg(&perm[acc0]));
-        if constexpr (BATCH) wfr[o] = (uint16_t)f;
-    }
-    if (acc1 != kNone) {
-        const uint32_t o = cnt + __popc(b0) + __popc(b1 & lt);
-        wbuf[o] = make_uint2(j, __ldg(&perm[acc1]));
-        if constexpr (BATCH) wfr[o] = (uint16_t)f;
+    uint32_t base = cnt;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        if (acc[k] != kNone) {
+            const uint32_t o = base + __popc(bal[k] & lt);
+            wbuf[o] = make_uint2(j, __ldg(&perm[acc[k]]));
+            if constexpr (BATCH) wfr[o] = (uint16_t)f;
+        }
+        base += __popc(bal[k]);
     }
     cnt += tot;
     __syncwarp();
@@ -171,9 +176,137 @@ __device__ __forceinline__ uint32_t range_argmin(uint32_t a, uint32_t b, uint32_
     return k;
 }
 
+// The eye a traversal works on.
+struct Eye {
+    float x, y, z, tau;
+    uint32_t r, c;  // shift and brev(2^32 - r)
+};
+
+// What one lane's visit produces: up to W children to push (node, argmin of its range
+// minimum) and up to W accepted leaves.
+template <int W>
+struct Visit {
+    bool go[W];
+    uint32_t node[W], karg[W], acc[W];
+};
+
+// Test one child slot: an internal child (range of more than one leaf) survives unless
+// its range minimum at argmin k culls it; the box is (lo, imax, hi).
+__device__ __forceinline__ bool survives(const Eye &E, const float4 &lo, const float4 &hi, uint32_t k) {
+    float den, rhs;
+    hrr_node_bound(E.tau, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w, E.x, E.y, E.z, den, rhs);
+    return !hrr_node_culls(__brev(k) + E.r, den, rhs);
+}
+
+// A visit of binary node `node`: its 64-byte record holds both children (box low corner
+// with the maximum intensity, box high corner with `split` / the range's other end).
+template <int VARIANT>
+__device__ __forceinline__ void visit(const float4 *nodes, uint32_t n_lights, uint32_t node, uint32_t kmin,
+                                      const Eye &E, unsigned long long *flags, Visit<2> &V) {
+    float4 q0, q1, q2, q3;
+    load32(&nodes[4 * (size_t)node], q0, q1);
+    load32(&nodes[4 * (size_t)node + 2], q2, q3);
+    const uint32_t split = __float_as_uint(q1.w);
+    const uint32_t other = __float_as_uint(q3.w);
+    const uint32_t first = min(node, other), last = max(node, other);
+    if (last >= n_lights || split - first >= last - first) {  // needs first <= split < last
+        atomicOr(flags, HRR_FLAG_TOPOLOGY);                    // corrupt record
+        return;
+    }
+    const bool int0 = first != split, int1 = split + 1u != last;
+    const bool kin0 = kmin <= split;
+    uint32_t knew = kNone;
+    if (kin0 ? int1 : int0)
+        knew = range_argmin<VARIANT>(kin0 ? split + 1u : first, kin0 ? last + 1u : split + 1u, E.r, E.c);
+    V.karg[0] = kin0 ? kmin : knew;
+    V.karg[1] = kin0 ? knew : kmin;
+    V.node[0] = split;
+    V.node[1] = split + 1u;
+    V.go[0] = int0 && survives(E, q0, q1, V.karg[0]);
+    V.go[1] = int1 && survives(E, q2, q3, V.karg[1]);
+    if (!int0 || !int1) {  // leaf children: one test site, a second for two leaves
+        const uint32_t i = !int0 ? split : last;
+        const float4 ql = !int0 ? q0 : q2;
+        if (hrr_leaf_accepts(__brev(i) + E.r, E.tau, ql.x, ql.y, ql.z, ql.w, E.x, E.y, E.z)) V.acc[0] = i;
+        if (!int0 && !int1 &&
+            hrr_leaf_accepts(__brev(last) + E.r, E.tau, q2.x, q2.y, q2.z, q2.w, E.x, E.y, E.z))
+            V.acc[1] = last;
+    }
+}
+
+// A visit of node g read with width four: its 128-byte record holds the four grandchild
+// slots [first, s0], [s0 + 1, split], [split + 1, s1], [s1 + 1, last] (a leaf child fills its
+// first slot and leaves the second empty). The parent's argmin lies in one child; one range
+// minimum gives the other child's, and one more per internal child splits it between that
+// child's two slots.
+template <int VARIANT>
+__device__ __forceinline__ void visit(const float4 *wide, uint32_t n_lights, uint32_t g, uint32_t kmin,
+                                      const Eye &E, unsigned long long *flags, Visit<4> &V) {
+    float4 q[8];
+    load32(&wide[8 * (size_t)g], q[0], q[1]);
+    load32(&wide[8 * (size_t)g + 2], q[2], q[3]);
+    load32(&wide[8 * (size_t)g + 4], q[4], q[5]);
+    load32(&wide[8 * (size_t)g + 6], q[6], q[7]);
+    const uint32_t s0 = __float_as_uint(q[1].w), split = __float_as_uint(q[3].w);
+    const uint32_t s1 = __float_as_uint(q[5].w), other = __float_as_uint(q[7].w);
+    const uint32_t first = min(g, other), last = max(g, other);
+    const bool c0int = first != split, c1int = split + 1u != last;
+    // first <= s0 <= split < last, split < s1 <= last, and an internal child's split inside it
+    // (so every internal slot is a node below g, with a record)
+    if (last >= n_lights || s0 - first > split - first || split - first >= last - first ||
+        s1 - split - 1u > last - split - 1u || (c0int && s0 == split) || (c1int && s1 == last)) {
+        atomicOr(flags, HRR_FLAG_TOPOLOGY);  // corrupt record
+        return;
+    }
+    const bool kin0 = kmin <= split;
+    const uint32_t kc = range_argmin<VARIANT>(kin0 ? split + 1u : first, kin0 ? last + 1u : split + 1u, E.r, E.c);
+    const uint32_t kA = kin0 ? kmin : kc, kB = kin0 ? kc : kmin;  // argmins of children 0 and 1
+    uint32_t k[4] = {kA, kA, kB, kB};
+    if (c0int) {
+        const bool in0 = kA <= s0;
+        const uint32_t kx = range_argmin<VARIANT>(in0 ? s0 + 1u : first, in0 ? split + 1u : s0 + 1u, E.r, E.c);
+        k[0] = in0 ? kA : kx;
+        k[1] = in0 ? kx : kA;
+    }
+    if (c1int) {
+        const bool in2 = kB <= s1;
+        const uint32_t ky = range_argmin<VARIANT>(in2 ? s1 + 1u : split + 1u, in2 ? last + 1u : s1 + 1u, E.r, E.c);
+        k[2] = in2 ? kB : ky;
+        k[3] = in2 ? ky : kB;
+    }
+    const uint32_t a[4] = {first, s0 + 1u, split + 1u, s1 + 1u};
+    const uint32_t b[4] = {s0, split, s1, last};  // inclusive; a > b: an empty slot
+    V.node[0] = s0;
+    V.node[1] = s0 + 1u;
+    V.node[2] = s1;
+    V.node[3] = s1 + 1u;
+    bool any_leaf = false;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        V.karg[t] = k[t];
+        V.go[t] = a[t] < b[t] && survives(E, q[2 * t], q[2 * t + 1], k[t]);
+        any_leaf |= a[t] == b[t];
+    }
+    if (any_leaf) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (a[t] == b[t] &&
+                hrr_leaf_accepts(__brev(a[t]) + E.r, E.tau, q[2 * t].x, q[2 * t].y, q[2 * t].z, q[2 * t].w, E.x,
+                                 E.y, E.z))
+                V.acc[t] = a[t];
+    }
+}
+
 // The traversal over the frames F (F[0] alone for a single frame).
-template <int VARIANT, bool BATCH>
+template <int VARIANT, bool BATCH, int W, int RING, int THREADS>
 __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
+    constexpr int kWarps = THREADS / 32;
+    constexpr uint32_t kRing = RING;
+    constexpr uint32_t kRingMask = kRing - 1;
+    // a step pushes at most 32 W entries; making room for them must only move entries that
+    // are resident (see the spill below), which needs kRing >= 32 W + 31
+    static_assert((kRing & kRingMask) == 0 && kRing >= 32 * W + 32, "ring size");
+    static_assert(kBuf >= 32 * W, "output staging buffer");
     __shared__ uint2 buf[kWarps][kBuf];
     __shared__ uint16_t buf_frame[BATCH ? kWarps : 1][BATCH ? kBuf : 1];
     __shared__ uint2 ring_all[kWarps][kRing];  // (node, argmin of its range minimum)
@@ -190,15 +323,15 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
 
     for (;;) {
         // The warp's next eye (warp-uniform from here on).
-        unsigned long long g = 0;
-        if (lane == 0) g = atomicAdd(Lc.cursor, 1ull);
-        g = __shfl_sync(0xFFFFFFFFu, g, 0);
-        if (g >= Lc.total) break;
-        if constexpr (BATCH) {  // last frame whose cursor offset is <= g
+        unsigned long long gcur = 0;
+        if (lane == 0) gcur = atomicAdd(Lc.cursor, 1ull);
+        gcur = __shfl_sync(0xFFFFFFFFu, gcur, 0);
+        if (gcur >= Lc.total) break;
+        if constexpr (BATCH) {  // last frame whose cursor offset is <= gcur
             uint32_t lo = 0, hi = Lc.n_frames - 1;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi + 1) >> 1;
-                if (frame_at<BATCH>(F, mid).cursor_begin <= g) lo = mid;
+                if (frame_at<BATCH>(F, mid).cursor_begin <= gcur) lo = mid;
                 else hi = mid - 1;
             }
             if (lo != f && visit_acc) {
@@ -209,27 +342,32 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
         }
         const Frame &fr = frame_at<BATCH>(F, f);
         const float4 *nodes = fr.nodes;
-        const float tau = fr.tau;
         const uint32_t n_lights = fr.n_lights;
-        const uint32_t j = fr.eye_begin + (uint32_t)(g - fr.cursor_begin);
-        const float ex = fr.ex[j], ey = fr.ey[j], ez = fr.ez[j];
+        const uint32_t j = fr.eye_begin + (uint32_t)(gcur - fr.cursor_begin);
+        Eye E;
+        E.x = fr.ex[j];
+        E.y = fr.ey[j];
+        E.z = fr.ez[j];
+        E.tau = fr.tau;
         const uint32_t tx = fr.px[j] % fr.tile_w, ty = fr.py[j] % fr.tile_h;
-        const uint32_t r = fr.tile[ty * fr.tile_w + tx] + fr.shift_offset;
-        if (n_lights == 1) {  // the root is a leaf (record 0, slot 0)
-            uint32_t acc = kNone;
+        E.r = fr.tile[ty * fr.tile_w + tx] + fr.shift_offset;
+        if (n_lights == 1) {  // the root is a leaf (record 0, slot 0, in either layout)
+            uint32_t acc[W];
+#pragma unroll
+            for (int t = 0; t < W; ++t) acc[t] = kNone;
             if (lane == 0) {
                 const float4 q0 = __ldg(&nodes[0]);
-                if (hrr_leaf_accepts(__brev(0u) + r, tau, q0.x, q0.y, q0.z, q0.w, ex, ey, ez)) acc = 0;
+                if (hrr_leaf_accepts(__brev(0u) + E.r, E.tau, q0.x, q0.y, q0.z, q0.w, E.x, E.y, E.z)) acc[0] = 0;
                 if (fr.eye_visits) fr.eye_visits[j] = 0;
             }
-            emit<BATCH>(F, wbuf, wfr, cnt, lane, f, j, acc, kNone);
+            emit<BATCH, W>(F, wbuf, wfr, cnt, lane, f, j, acc);
             continue;
         }
-        const uint32_t c = __brev(0u - r);
+        E.c = __brev(0u - E.r);
         // Stack: logical entries [0, S); the newest R of them are in the ring at index & mask,
         // the others in the spill area at their logical index.
         uint32_t S = 1, R = 1, visits = 0;
-        if (lane == 0) ring[0] = make_uint2(0u, range_argmin<VARIANT>(0u, n_lights, r, c));
+        if (lane == 0) ring[0] = make_uint2(0u, range_argmin<VARIANT>(0u, n_lights, E.r, E.c));
         __syncwarp();
         while (S > 0) {
             if (visits >= n_lights) {  // each internal node is visited at most once per eye
@@ -253,49 +391,28 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
             visits += m;
             __syncwarp();
 
-            bool go0 = false, go1 = false;
-            uint32_t k0 = 0, k1 = 0, split = 0;
-            uint32_t acc0 = kNone, acc1 = kNone;
-            if (active) {
-                const uint32_t node = e.x, kmin = e.y;
-                float4 q0, q1, q2, q3;
-                load_record(&nodes[4 * (size_t)node], q0, q1, q2, q3);
-                split = __float_as_uint(q1.w);
-                const uint32_t other = __float_as_uint(q3.w);
-                const uint32_t first = min(node, other), last = max(node, other);
-                if (last >= n_lights || split - first >= last - first) {  // needs first <= split < last
-                    atomicOr(Lc.flags, HRR_FLAG_TOPOLOGY);                   // corrupt record
-                } else {
-                    const bool int0 = first != split, int1 = split + 1u != last;
-                    const bool kin0 = kmin <= split;
-                    uint32_t knew = kNone;
-                    if (kin0 ? int1 : int0)
-                        knew = range_argmin<VARIANT>(kin0 ? split + 1u : first, kin0 ? last + 1u : split + 1u, r, c);
-                    k0 = kin0 ? kmin : knew;
-                    k1 = kin0 ? knew : kmin;
-                    float den0, rhs0, den1, rhs1;
-                    hrr_node_bound(tau, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q0.w, ex, ey, ez, den0, rhs0);
-                    hrr_node_bound(tau, q2.x, q2.y, q2.z, q3.x, q3.y, q3.z, q2.w, ex, ey, ez, den1, rhs1);
-                    go0 = int0 && !hrr_node_culls(__brev(k0) + r, den0, rhs0);
-                    go1 = int1 && !hrr_node_culls(__brev(k1) + r, den1, rhs1);
-                    if (!int0 || !int1) {  // leaf children: one test site, a second for two leaves
-                        const uint32_t i = !int0 ? split : last;
-                        const float4 ql = !int0 ? q0 : q2;
-                        if (hrr_leaf_accepts(__brev(i) + r, tau, ql.x, ql.y, ql.z, ql.w, ex, ey, ez)) acc0 = i;
-                        if (!int0 && !int1 &&
-                            hrr_leaf_accepts(__brev(last) + r, tau, q2.x, q2.y, q2.z, q2.w, ex, ey, ez))
-                            acc1 = last;
-                    }
-                }
+            Visit<W> V;
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                V.go[t] = false;
+                V.node[t] = 0;
+                V.karg[t] = 0;
+                V.acc[t] = kNone;
             }
+            if (active) visit<VARIANT>(nodes, n_lights, e.x, e.y, E, Lc.flags, V);
             // Push the surviving children as one compacted run.
-            const unsigned b0 = __ballot_sync(0xFFFFFFFFu, go0), b1 = __ballot_sync(0xFFFFFFFFu, go1);
-            const uint32_t n = __popc(b0) + __popc(b1);
+            unsigned bal[W];
+            uint32_t n = 0;
+#pragma unroll
+            for (int t = 0; t < W; ++t) {
+                bal[t] = __ballot_sync(0xFFFFFFFFu, V.go[t]);
+                n += __popc(bal[t]);
+            }
             if (n) {
                 if (R + n > kRing) {  // move the oldest resident entries to the spill area
                     const uint32_t s = (R + n - kRing + 31u) & ~31u;
                     const uint32_t base = S - R;
-                    if (base + s > Lc.spill_cap) {
+                    if (base + s > Lc.spill_cap) {  // cannot happen: the area holds the bound
                         if (lane == 0) atomicOr(Lc.flags, HRR_FLAG_STACK);
                         break;
                     }
@@ -304,14 +421,20 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
                     R -= s;
                     __syncwarp();
                 }
-                if (go0) ring[(S + __popc(b0 & lt)) & kRingMask] = make_uint2(split, k0);
-                if (go1) ring[(S + __popc(b0) + __popc(b1 & lt)) & kRingMask] = make_uint2(split + 1u, k1);
+                uint32_t pos = S;
+#pragma unroll
+                for (int t = 0; t < W; ++t) {
+                    if (V.go[t]) ring[(pos + __popc(bal[t] & lt)) & kRingMask] = make_uint2(V.node[t], V.karg[t]);
+                    pos += __popc(bal[t]);
+                }
                 S += n;
                 R += n;
                 __syncwarp();
             }
-            if (__any_sync(0xFFFFFFFFu, (acc0 & acc1) != kNone))
-                emit<BATCH>(F, wbuf, wfr, cnt, lane, f, j, acc0, acc1);
+            bool any_acc = false;
+#pragma unroll
+            for (int t = 0; t < W; ++t) any_acc |= V.acc[t] != kNone;
+            if (__any_sync(0xFFFFFFFFu, any_acc)) emit<BATCH, W>(F, wbuf, wfr, cnt, lane, f, j, V.acc);
         }
         if (lane == 0) {
             uint32_t *ev = frame_at<BATCH>(F, f).eye_visits;
@@ -329,54 +452,93 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
 
 // A single frame travels as a plain kernel parameter; a batch's frames as a grid-constant
 // array (indexed by the frame a warp is on).
-template <int VARIANT>
-__global__ void __launch_bounds__(kThreads, HRR_CULL_MIN_BLOCKS)
+template <int VARIANT, int W, int RING, int THREADS>
+__global__ void __launch_bounds__(THREADS, min_blocks<W>(THREADS))
 cull_single_kernel(const Launch Lc, const Frame fr) {
-    traverse<VARIANT, false>(Lc, &fr);
+    traverse<VARIANT, false, W, RING, THREADS>(Lc, &fr);
+}
+
+template <int VARIANT, int W, int RING, int THREADS>
+__global__ void __launch_bounds__(THREADS, min_blocks<W>(THREADS))
+cull_batch_kernel(const __grid_constant__ Launch Lc, const __grid_constant__ FrameArray<kMaxFrames> FA) {
+    traverse<VARIANT, true, W, RING, THREADS>(Lc, FA.f);
+}
+
+// ------------------------------------------------------------------------------------
+// Instantiations and their dispatch
+// ------------------------------------------------------------------------------------
+
+// One compiled form of the traversal: range-minimum variant, node width, ring entries per
+// warp and threads per block, with its single-frame and batched kernels.
+struct CullKernel {
+    int variant, width, ring, threads;
+    const void *single, *batch;
+    int occ[2];  // resident blocks per SM (single, batched), 0 until first asked
+};
+
+template <int VARIANT, int W, int RING, int THREADS>
+CullKernel cull_entry() {
+    return {VARIANT, W, RING, THREADS, reinterpret_cast<const void *>(cull_single_kernel<VARIANT, W, RING, THREADS>),
+            reinterpret_cast<const void *>(cull_batch_kernel<VARIANT, W, RING, THREADS>), {0, 0}};
 }
 
 template <int VARIANT>
-__global__ void __launch_bounds__(kThreads, HRR_CULL_BATCH_MIN_BLOCKS)
-cull_batch_kernel(const __grid_constant__ Launch Lc, const __grid_constant__ FrameArray<kMaxFrames> FA) {
-    traverse<VARIANT, true>(Lc, FA.f);
+void add_entries(std::vector<CullKernel> &v) {
+    v.push_back(cull_entry<VARIANT, 2, 256, 256>());
+    v.push_back(cull_entry<VARIANT, 2, 128, 256>());
+    v.push_back(cull_entry<VARIANT, 2, 256, 128>());
+    v.push_back(cull_entry<VARIANT, 2, 128, 128>());
+    v.push_back(cull_entry<VARIANT, 4, 256, 256>());
+    v.push_back(cull_entry<VARIANT, 4, 512, 256>());
+    v.push_back(cull_entry<VARIANT, 4, 256, 128>());
+    v.push_back(cull_entry<VARIANT, 4, 512, 128>());
 }
 
-template <int VARIANT, bool BATCH>
-const void *kernel_fn() {
-    if constexpr (BATCH) return reinterpret_cast<const void *>(cull_batch_kernel<VARIANT>);
-    else return reinterpret_cast<const void *>(cull_single_kernel<VARIANT>);
+std::vector<CullKernel> &cull_kernels() {
+    static std::vector<CullKernel> v = [] {
+        std::vector<CullKernel> t;
+        add_entries<0>(t);
+        add_entries<2>(t);
+        return t;
+    }();
+    return v;
 }
 
-// Resident blocks per SM of a traversal kernel (one cache per instantiation).
-template <int VARIANT, bool BATCH>
-int occupancy() {
-    static int n = 0;
+// The compiled form for a normalised tuning (nullptr if there is none).
+CullKernel *cull_kernel_for(const hrr_tuning &t) {
+    for (CullKernel &k : cull_kernels())
+        if (k.variant == t.rangemin_variant && k.width == (int)t.node_width && k.ring == (int)t.ring_entries &&
+            k.threads == (int)t.threads_per_block)
+            return &k;
+    return nullptr;
+}
+
+int cull_occupancy(CullKernel &k, bool batch) {
+    int &n = k.occ[batch ? 1 : 0];
     if (!n) {
         int m = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, kernel_fn<VARIANT, BATCH>(), kThreads, 0) !=
-                cudaSuccess || m < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, batch ? k.batch : k.single, k.threads, 0) !=
+                cudaSuccess || m < 1) {
+            cudaGetLastError();
             m = 1;
+        }
         n = m;
     }
     return n;
 }
 
-template <bool BATCH>
-int occupancy_of(int variant) {
-    return variant == 0 ? occupancy<0, BATCH>() : occupancy<2, BATCH>();
+cudaError_t launch_single(CullKernel &k, unsigned grid, const Launch &Lc, const Frame &fr, cudaStream_t st) {
+    Launch lc = Lc;
+    Frame f = fr;
+    void *args[] = {&lc, &f};
+    return cudaLaunchKernel(k.single, dim3(grid), dim3(k.threads), args, 0, st);
 }
 
-cudaError_t launch_single(const hrr_tuning &tn, unsigned grid, const Launch &Lc, const Frame &fr, cudaStream_t st) {
-    if (tn.rangemin_variant == 0) cull_single_kernel<0><<<grid, kThreads, 0, st>>>(Lc, fr);
-    else cull_single_kernel<2><<<grid, kThreads, 0, st>>>(Lc, fr);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_batch(const hrr_tuning &tn, unsigned grid, const Launch &Lc, const FrameArray<kMaxFrames> &fa,
+cudaError_t launch_batch(CullKernel &k, unsigned grid, const Launch &Lc, const FrameArray<kMaxFrames> &fa,
                          cudaStream_t st) {
-    if (tn.rangemin_variant == 0) cull_batch_kernel<0><<<grid, kThreads, 0, st>>>(Lc, fa);
-    else cull_batch_kernel<2><<<grid, kThreads, 0, st>>>(Lc, fa);
-    return cudaGetLastError();
+    Launch lc = Lc;
+    void *args[] = {&lc, const_cast<FrameArray<kMaxFrames> *>(&fa)};
+    return cudaLaunchKernel(k.batch, dim3(grid), dim3(k.threads), args, 0, st);
 }
 
 }  // namespace

@@ -81,7 +81,16 @@ struct hrr_tree {
     uint32_t height = 0;
     hrr_node *nodes = nullptr;  // n - 1 records (one record with the single leaf if n == 1)
     uint32_t *perm = nullptr;   // n
+    // The same hierarchy read with nodes of width four: for every internal node g a
+    // 128-byte record of its four grandchild slots (hrr_widen_enqueue), at index g; a
+    // traversal of width four reads the even-depth ones only. One record (the leaf in
+    // slot 0) when n == 1.
+    float4 *wide = nullptr;
 };
+
+// Fill tree->wide from tree->nodes (one thread per internal node); skipped when *flags
+// holds HRR_FLAG_NONFINITE (a failed refit leaves the hierarchy as it was).
+cudaError_t hrr_widen_enqueue(hrr_tree *tree, const unsigned long long *flags, cudaStream_t st);
 
 // Layer (sample mod d) of a w x h x d tile: the shifts one culling pass uses.
 inline const uint32_t *hrr_tile_layer(const uint32_t *tile, uint32_t w, uint32_t h, uint32_t d,
@@ -131,33 +140,56 @@ struct hrr_cull_frame_t {
     unsigned long long cursor_begin; // where the frame's eyes start on the launch's cursor
 };
 
-// Launch parameters with the library defaults filled in (nothing to fill in today).
-inline hrr_tuning hrr_tuning_normalized(hrr_tuning t) { return t; }
+// Traversal defaults: node width, shared-memory stack ring per warp, threads per block.
+#define HRR_DEFAULT_NODE_WIDTH 2u
+#define HRR_DEFAULT_RING 256u
+#define HRR_DEFAULT_THREADS 256u
+
+// Launch parameters with the library defaults filled in.
+inline hrr_tuning hrr_tuning_normalized(hrr_tuning t) {
+    if (!t.node_width) t.node_width = HRR_DEFAULT_NODE_WIDTH;
+    if (!t.ring_entries) t.ring_entries = HRR_DEFAULT_RING;
+    if (!t.threads_per_block) t.threads_per_block = HRR_DEFAULT_THREADS;
+    return t;
+}
 inline hrr_tuning hrr_tuning_of(const hrr_cull_opts &o) {
     hrr_tuning t{};
     t.rangemin_variant = o.rangemin_variant;
     t.blocks_per_sm = o.blocks_per_sm;
+    t.node_width = o.node_width;
+    t.ring_entries = o.ring_entries;
+    t.threads_per_block = o.threads_per_block;
     return hrr_tuning_normalized(t);
 }
-inline bool hrr_tuning_valid(const hrr_tuning &t) {
-    return (t.rangemin_variant == 0 || t.rangemin_variant == 2) && t.blocks_per_sm <= 64;
+// Every combination that has a compiled traversal (zero fields stand for the defaults).
+inline bool hrr_tuning_valid(const hrr_tuning &t0) {
+    const hrr_tuning t = hrr_tuning_normalized(t0);
+    if ((t.rangemin_variant != 0 && t.rangemin_variant != 2) || t.blocks_per_sm > 64) return false;
+    if (t.threads_per_block != 128 && t.threads_per_block != 256) return false;
+    if (t.node_width == 2) return t.ring_entries == 128 || t.ring_entries == 256;
+    if (t.node_width == 4) return t.ring_entries == 256 || t.ring_entries == 512;
+    return false;
 }
 
-// The traversal (hrr_cull_kernel.cuh). Threads per block of its persistent grid, and frames of one
-// batched launch (their descriptors are kernel parameters: 128 x 128 bytes):
-#define HRR_CULL_THREADS 256
+// The traversal (hrr_cull_kernel.cuh). Frames of one batched launch (their descriptors are
+// kernel parameters: 128 x 128 bytes):
 #define HRR_CULL_MAX_FRAMES 128u
 // Blocks of a traversal launch over `total` eyes (a whole number per SM, at most one warp per
-// eye), for the single-frame or the batched kernel.
+// eye), for the single-frame or the batched kernel of a (normalised, valid) tuning.
 unsigned hrr_cull_grid(int sm_count, const hrr_tuning &tuning, bool batch, unsigned long long total);
-// Stack entries per warp that the spill area must hold for trees of the given height, and
-// the area's entries (8 bytes each) for a grid.
-uint32_t hrr_cull_spill_cap(uint32_t height);
-size_t hrr_cull_spill_entries(unsigned grid, uint32_t height);
+// Resident blocks per SM of the traversal kernel of a (normalised, valid) tuning.
+int hrr_cull_max_blocks(const hrr_tuning &tuning, bool batch);
+// Stack entries per warp that the spill area must hold for trees of the given height read
+// with the given node width (the proven bound plus a margin), and the area's entries
+// (8 bytes each) for a grid of the tuning's blocks.
+uint32_t hrr_cull_spill_cap(uint32_t height, uint32_t width);
+size_t hrr_cull_spill_entries(unsigned grid, uint32_t height, const hrr_tuning &tuning);
+// The node records a traversal of the tuning's width reads (tree->nodes or tree->wide).
+const float4 *hrr_cull_records(const hrr_tree *tree, const hrr_tuning &tuning);
 // Enqueue one batched traversal over n_frames <= HRR_CULL_MAX_FRAMES frames (host array, copied
 // into the launch) on st; a no-op when total == 0. The cursor and flags must be zero when the
 // kernel starts. spill holds hrr_cull_spill_entries(grid, height) entries for the tallest tree
-// of the frames, spill_cap = hrr_cull_spill_cap(height).
+// of the frames, spill_cap = hrr_cull_spill_cap(height, tuning.node_width).
 cudaError_t hrr_cull_batch_enqueue(unsigned grid, const hrr_cull_frame_t *frames, uint32_t n_frames,
                                    unsigned long long total, unsigned long long *cursor,
                                    unsigned long long *flags, void *spill, uint32_t spill_cap,

@@ -25,7 +25,7 @@
 
 namespace {
 
-constexpr int kThreads = HRR_CULL_THREADS;
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kBuf = 128;       // staged output entries per warp
 constexpr uint32_t kRing = 256;  // stack entries per warp in shared memory
@@ -281,7 +281,7 @@ int hrr_cull_samples_impl(hrr_ctx *ctx, const hrr_eyes &E, uint32_t n_eyes, cons
         const unsigned long long needed = ((unsigned long long)n_eyes + kWarps - 1) / kWarps;
         const unsigned grid =
             (unsigned)std::max<unsigned long long>(1ull, std::min<unsigned long long>((unsigned long long)per_sm * ctx->sm_count, needed));
-        const uint32_t spill_cap = hrr_cull_spill_cap(tree->height);
+        const uint32_t spill_cap = hrr_cull_spill_cap(tree->height, 2);  // binary records, two pushes a visit
         const size_t need = (size_t)grid * kWarps * spill_cap;
         if (need > ctx->spill_entries) {  // the stack spill area grows with the grid and tree height
             HRR_CUDA(ctx, cudaStreamSynchronize(st));

@@ -166,7 +166,7 @@ void admit(hrr_server *s) {
 bool ensure_spill(hrr_server *s, uint32_t height) {
     if (height <= s->spill_height && s->spill[0]) return true;
     for (int k = 0; k < kRing; ++k) cudaStreamSynchronize(s->slice_stream[k]);
-    const size_t bytes = hrr_cull_spill_entries(s->grid_max, height) * sizeof(uint2);
+    const size_t bytes = hrr_cull_spill_entries(s->grid_max, height, s->tuning) * sizeof(uint2);
     for (int k = 0; k < kRing; ++k) {
         if (s->spill[k]) cudaFree(s->spill[k]);
         s->spill[k] = nullptr;
@@ -232,7 +232,7 @@ bool enqueue_slice(hrr_server *s, int k) {
             } else {
                 if (hrr_refit_enqueue(const_cast<hrr_tree *>(j->desc.tree), j->desc.refit, scratch,
                                       s->dev_counts + kSlotWords * (size_t)j->slot + 2, st) == cudaSuccess)
-                    s->launches += j->desc.tree->n > 1 ? 3 : 1;
+                    s->launches += j->desc.tree->n > 1 ? 4 : 2;
                 cudaFreeAsync(scratch, st);
             }
         }
@@ -261,7 +261,7 @@ bool enqueue_slice(hrr_server *s, int k) {
         d = hrr_cull_frame_t{};
         d.ex = j->desc.eyes.x; d.ey = j->desc.eyes.y; d.ez = j->desc.eyes.z;
         d.px = j->desc.eyes.px; d.py = j->desc.eyes.py;
-        d.nodes = reinterpret_cast<const float4 *>(j->desc.tree->nodes);
+        d.nodes = hrr_cull_records(j->desc.tree, s->tuning);
         d.perm = j->desc.tree->perm;
         d.tile = j->tile; d.tile_w = j->tile_w; d.tile_h = j->tile_h;
         d.pairs = j->pairs;
@@ -284,7 +284,8 @@ bool enqueue_slice(hrr_server *s, int k) {
     } else if (cursor) {
         const unsigned grid = hrr_cull_grid(s->sm_count, s->tuning, true, cursor);
         if (hrr_cull_batch_enqueue(grid, h, n, cursor, s->dev_misc + 2 * k, s->dev_misc + 2 * k + 1,
-                                   s->spill[k], hrr_cull_spill_cap(s->spill_height), s->tuning, st) == cudaSuccess)
+                                   s->spill[k], hrr_cull_spill_cap(s->spill_height, s->tuning.node_width), s->tuning,
+                                   st) == cudaSuccess)
             ++s->launches;
     }
     cudaMemcpyAsync(&s->host_flags[k], s->dev_misc + 2 * k + 1, sizeof(unsigned long long),
@@ -452,6 +453,8 @@ int hrr_server_submit(hrr_server *s, hrr_ctx *ctx, const hrr_job *job, uint64_t 
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job has a NULL or foreign tree, a bad tau or a NULL eye array");
     if (d.refit.x && (!d.refit.y || !d.refit.z || !d.refit.intensity))
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job refit lights are partly NULL");
+    if (!hrr_cull_records(d.tree, s->tuning))
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "job tree has no records of the server's node width");
     const uint32_t *tile = d.dev_tile;
     uint32_t tw = d.tile_w, th = d.tile_h;
     hrr_tile_buf *ctx_tile = nullptr;

@@ -15,9 +15,12 @@ class FakeCtx:
     def __init__(self):
         self.calls = []
 
-    def autotune(self, x, y, z, px, py, tree, tau, pairs):
+    def autotune_all(self, x, y, z, px, py, tree, tau, pairs):
         self.calls.append(int(x.numel()))
-        return {"rangemin_variant": 2, "blocks_per_sm": 5}, 1.25
+        best = {"rangemin_variant": 2, "blocks_per_sm": 5, "node_width": 4, "ring_entries": 256,
+                "threads_per_block": 128}
+        other = dict(best, node_width=2, blocks_per_sm=6)
+        return [(other, 1.5), (best, 1.25), (dict(best, rangemin_variant=0), 1.3)]
 
 
 def _eyes(n):
@@ -37,8 +40,10 @@ def test_tune_once_then_cached(tmp_path):
     at = Autotuner(ctx, cache_path=path, sample_eyes=1000)
     e = at.tune(*_eyes(5000), None, 1.0, n_lights=70000)
     assert ctx.calls == [1000]  # tuned on the bounded sample
-    assert Autotuner.launch_fields(e) == {"rangemin_variant": 2, "blocks_per_sm": 5}
-    assert e["sample_ms"] == 1.25
+    assert Autotuner.launch_fields(e) == {"rangemin_variant": 2, "blocks_per_sm": 5, "node_width": 4,
+                                          "ring_entries": 256, "threads_per_block": 128}
+    assert e["sample_ms"] == 1.25  # the fastest candidate of the table
+    assert len(at.last_table) == 3
     again = at.tune(*_eyes(6000), None, 1.0, n_lights=66000)  # same class
     assert again == e and ctx.calls == [1000]
     at.tune(*_eyes(500), None, 1.0, n_lights=70000)  # new class, smaller than the sample

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import run_cull, sorted_pairs, upload_scene
+from gpu_util import oracle_hier, run_cull, sorted_pairs, upload_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -31,29 +31,36 @@ def _gpu(ctx, s, **kw):
     return res
 
 
+FORMS = [{"node_width": w, "ring_entries": r, "threads_per_block": th}
+         for w, rings in ((2, (128, 256)), (4, (256, 512))) for r in rings for th in (128, 256)]
+
+
 @pytest.mark.parametrize("variant", [0, 2])
-def test_uniform_tiny_scene_equals_flat(ctx, variant):
-    # 1024 eyes x 4096 lights, 32x32 tile, tau for ~32 accepted per eye
+@pytest.mark.parametrize("form", FORMS, ids=lambda f: "w{node_width}r{ring_entries}t{threads_per_block}".format(**f))
+def test_uniform_tiny_scene_equals_flat(ctx, variant, form):
+    # 1024 eyes x 4096 lights, 32x32 tile, tau for ~32 accepted per eye, in every compiled
+    # form of the traversal (node width, stack ring, threads per block)
     s = synth.scene_uniform()
-    st, cnt, pairs, vis = _gpu(ctx, s, visits=True, variant=variant)
+    st, cnt, pairs, vis = _gpu(ctx, s, visits=True, tuning=dict(form, rangemin_variant=variant))
     assert st == 0
     t = oracle.Tree(s.light_pos, s.intensity)
     flat = oracle.cull_flat(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
     assert np.array_equal(sorted_pairs(pairs), sorted_pairs(flat["pairs"]))
-    hier = oracle.cull_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
+    hier = oracle_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau, width=form["node_width"])
     assert np.array_equal(vis, hier["visits"].astype(np.uint32))
     v_total, acc = ctx.last_cull_stats()
     assert v_total == hier["total_visits"] and acc == cnt == len(flat["pairs"])
 
 
-def test_ragged_frame_equals_oracle(ctx):
+@pytest.mark.parametrize("width", [2, 4])
+def test_ragged_frame_equals_oracle(ctx, width):
     # eye count not a multiple of the warp or block size, light count not a power of two
     s = synth.scene_frame(width=257, height=131, n_lights=50021, tile_w=64, tile_h=64,
                           target=64.0, seed=7)
-    st, cnt, pairs, vis = _gpu(ctx, s, visits=True)
+    st, cnt, pairs, vis = _gpu(ctx, s, visits=True, tuning={"node_width": width})
     assert st == 0
     t = oracle.Tree(s.light_pos, s.intensity)
-    hier = oracle.cull_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
+    hier = oracle_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau, width=width)
     assert np.array_equal(sorted_pairs(pairs), sorted_pairs(hier["pairs"]))
     assert np.array_equal(vis, hier["visits"].astype(np.uint32))
     # flat brute force on a sample of eyes (hier == flat is pinned on the CPU)
@@ -74,7 +81,7 @@ def test_full_size_frame_sampled(ctx):
     assert 20 * n_e < cnt < 200 * n_e  # about 64 accepted per eye
     ids = np.unique(np.concatenate([np.arange(0, n_e, n_e // 301), [n_e - 1]])).astype(np.uint32)
     t = oracle.Tree(s.light_pos, s.intensity)
-    hier = oracle.cull_hier(t, s.eye_pos[ids], s.px[ids], s.py[ids], s.tile, s.tau, eye_ids=ids)
+    hier = oracle_hier(t, s.eye_pos[ids], s.px[ids], s.py[ids], s.tile, s.tau, eye_ids=ids)
     got = pairs[np.isin(pairs[:, 0], ids)]
     assert np.array_equal(sorted_pairs(got), sorted_pairs(hier["pairs"]))
     assert np.array_equal(vis[ids], hier["visits"].astype(np.uint32))
@@ -107,23 +114,24 @@ def test_largest_batch_frame_sampled(ctx):
     got = sel.cpu().numpy().view(np.uint32)
     del pairs, sel
     t = oracle.Tree(s.light_pos, s.intensity, topology="cost")
-    hier = oracle.cull_hier(t, s.eye_pos[ids], s.px[ids], s.py[ids], s.tile, s.tau, eye_ids=ids)
+    hier = oracle_hier(t, s.eye_pos[ids], s.px[ids], s.py[ids], s.tile, s.tau, eye_ids=ids)
     assert np.array_equal(sorted_pairs(got), sorted_pairs(hier["pairs"]))
     assert np.array_equal(vis.cpu().numpy().view(np.uint32)[ids], hier["visits"].astype(np.uint32))
 
 
-@pytest.mark.parametrize("n_lights", [1, 2, 3, 33])
-def test_tiny_light_sets(ctx, n_lights):
+@pytest.mark.parametrize("width", [2, 4])
+@pytest.mark.parametrize("n_lights", [1, 2, 3, 4, 5, 33])
+def test_tiny_light_sets(ctx, n_lights, width):
     s = dict(synth.scene_uniform(n_lights=64, grid_w=16, grid_h=8, tile_w=8, tile_h=8,
                                  target=4.0, seed=9))
     s["light_pos"] = s["light_pos"][:n_lights]
     s["intensity"] = s["intensity"][:n_lights]
     s["tau"] = np.float32(s["tau"] * 20)
-    st, cnt, pairs, vis = _gpu(ctx, s, visits=True)
+    st, cnt, pairs, vis = _gpu(ctx, s, visits=True, tuning={"node_width": width})
     assert st == 0
     t = oracle.Tree(s["light_pos"], s["intensity"])
     flat = oracle.cull_flat(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"])
-    hier = oracle.cull_hier(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"])
+    hier = oracle_hier(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"], width=width)
     assert np.array_equal(sorted_pairs(pairs), sorted_pairs(flat["pairs"]))
     assert np.array_equal(vis, hier["visits"].astype(np.uint32))
 

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import dev, run_cull, sorted_pairs, upload_scene
+from gpu_util import dev, oracle_hier, run_cull, sorted_pairs, upload_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -20,33 +20,43 @@ def ctx():
     c.close()
 
 
-def test_nothing_culled_visits_every_node(ctx):
-    # full traversal of a 2^18-light tree: the pending frontier exceeds 256 nodes
+@pytest.mark.parametrize("width", [2, 4])
+def test_nothing_culled_visits_every_node(ctx, width):
+    # full traversal of a 2^18-light tree: the pending frontier exceeds the ring, so the
+    # stack spills to global memory and comes back (its bound sizes the spill area)
     s = dict(synth.scene_frame(width=8, height=6, n_lights=1 << 18, tile_w=8, tile_h=8, seed=21))
     s["tau"] = np.float32(1e30)
     g = upload_scene(s)
     ctx.set_shift_tile(s["tile"])
     tree = ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"])
     n_e, n_l = len(s["eye_pos"]), len(s["light_pos"])
-    st, cnt, pairs, vis = run_cull(ctx, g, tree, float(s["tau"]), cap=n_e * n_l, visits=True)
+    st, cnt, pairs, vis = run_cull(ctx, g, tree, float(s["tau"]), cap=n_e * n_l, visits=True,
+                                   tuning={"node_width": width})
     tree.free()
     assert st == 0 and cnt == n_e * n_l
-    assert np.all(vis == n_l - 1)
+    if width == 2:
+        assert np.all(vis == n_l - 1)
+    else:  # every even-depth internal node
+        t = oracle.Tree(s["light_pos"], s["intensity"])
+        one = oracle_hier(t, s["eye_pos"][:1], s["px"][:1], s["py"][:1], s["tile"], s["tau"], width=4)
+        assert np.all(vis == int(one["visits"][0])) and n_l // 4 < int(one["visits"][0]) < n_l // 2
     p = sorted_pairs(pairs)
     assert np.array_equal(p[:, 0], np.repeat(np.arange(n_e, dtype=np.uint32), n_l))
     assert np.array_equal(p[:, 1], np.tile(np.arange(n_l, dtype=np.uint32), n_e))
 
 
-def test_thousands_accepted_per_eye_equal_oracle(ctx):
+@pytest.mark.parametrize("width", [2, 4])
+def test_thousands_accepted_per_eye_equal_oracle(ctx, width):
     s = synth.scene_frame(width=9, height=5, n_lights=1 << 18, tile_w=8, tile_h=8, target=6000.0, seed=22)
     g = upload_scene(s)
     ctx.set_shift_tile(s.tile)
     tree = ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"])
-    st, cnt, pairs, vis = run_cull(ctx, g, tree, float(s.tau), cap=len(s.eye_pos) * 20000, visits=True)
+    st, cnt, pairs, vis = run_cull(ctx, g, tree, float(s.tau), cap=len(s.eye_pos) * 20000, visits=True,
+                                   tuning={"node_width": width})
     tree.free()
     assert st == 0
     t = oracle.Tree(s.light_pos, s.intensity)
-    hier = oracle.cull_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
+    hier = oracle_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau, width=width)
     assert cnt == len(hier["pairs"]) and cnt > 1000 * len(s.eye_pos)
     assert np.array_equal(sorted_pairs(pairs), sorted_pairs(hier["pairs"]))
     assert np.array_equal(vis, hier["visits"].astype(np.uint32))

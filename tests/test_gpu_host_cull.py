@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import sorted_pairs
+from gpu_util import oracle_hier, sorted_pairs
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,7 @@ def test_ragged_frame_equals_oracle(ctx, pinned):
     tree.free()
     assert st == 0
     t = oracle.Tree(s["light_pos"], s["intensity"])
-    hier = oracle.cull_hier(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"])
+    hier = oracle_hier(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"])
     got = pairs[:cnt].numpy().view(np.uint32)
     assert np.array_equal(sorted_pairs(got), sorted_pairs(hier["pairs"]))
 
@@ -90,7 +90,7 @@ def test_eight_slices_equal_device_cull_and_oracle(ctx):
     assert got[:, 0].max() < n_e and np.bincount(got[:, 0], minlength=n_e).sum() == cnt
     ids = np.unique(np.concatenate([np.arange(0, n_e, n_e // 97), [n_e - 1]])).astype(np.uint32)
     t = oracle.Tree(s["light_pos"], s["intensity"], topology="cost")
-    hier = oracle.cull_hier(t, s["eye_pos"][ids], s["px"][ids], s["py"][ids], s["tile"], s["tau"], eye_ids=ids)
+    hier = oracle_hier(t, s["eye_pos"][ids], s["px"][ids], s["py"][ids], s["tile"], s["tau"], eye_ids=ids)
     assert np.array_equal(sorted_pairs(got[np.isin(got[:, 0], ids)]), sorted_pairs(hier["pairs"]))
     tree.free()
 

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import dev, run_cull, sorted_pairs, upload_scene
+from gpu_util import dev, oracle_hier, run_cull, sorted_pairs, upload_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -67,7 +67,7 @@ def test_refit_equals_oracle_and_culls_exactly(ctx, n_lights):
     st, cnt, pairs, vis = run_cull(ctx, g, tree, float(s.tau), visits=True)
     assert st == 0
     flat = oracle.cull_flat(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
-    hier = oracle.cull_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
+    hier = oracle_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
     assert np.array_equal(sorted_pairs(pairs), sorted_pairs(flat["pairs"]))
     assert np.array_equal(vis, hier["visits"].astype(np.uint32))
     tree.free()

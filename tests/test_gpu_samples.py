@@ -33,7 +33,9 @@ def _separate(ctx, g, tree, tau, offsets, cap, sample_indices=None):
     pairs = torch.empty((cap, 2), dtype=torch.int32, device=dev())
     for s, off in enumerate(offsets):
         si = s if sample_indices is None else sample_indices[s]
-        st, cnt = ctx.cull(*_eyes(g), tree, tau, pairs, shift_offset=int(off) & 0xFFFFFFFF, sample_index=si)
+        # binary records: the one-traversal samples kernel counts binary node visits
+        st, cnt = ctx.cull(*_eyes(g), tree, tau, pairs, shift_offset=int(off) & 0xFFFFFFFF, sample_index=si,
+                           tuning={"node_width": 2})
         assert st == 0
         out.append(sorted_pairs(pairs[:cnt].cpu().numpy().view(np.uint32)))
         visits += ctx.last_cull_stats()[0]
@@ -162,7 +164,7 @@ def test_full_frame_four_samples(ctx):
     single = torch.empty((cap, 2), dtype=torch.int32, device=dev())
     total = 0
     for k, off in enumerate(offsets):
-        st1, cnt = ctx.cull(*_eyes(g), tree, float(s.tau), single, shift_offset=off)
+        st1, cnt = ctx.cull(*_eyes(g), tree, float(s.tau), single, shift_offset=off, tuning={"node_width": 2})
         assert st1 == 0 and cnt == counts[k]
         assert torch.equal(keys(pairs[k, :cnt]), keys(single[:cnt]))
         total += ctx.last_cull_stats()[0]

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import dev, run_cull, sorted_pairs, upload_scene
+from gpu_util import dev, oracle_hier, run_cull, sorted_pairs, upload_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +41,7 @@ def test_samples_use_their_layer(env):
     for n in (0, 1, 3, 6):
         pairs, vis = _plain(ctx, g, tree, float(s.tau), n)
         flat = oracle.cull_flat(t, s.eye_pos, s.px, s.py, t3, s.tau, sample_index=n)
-        hier = oracle.cull_hier(t, s.eye_pos, s.px, s.py, t3, s.tau, sample_index=n)
+        hier = oracle_hier(t, s.eye_pos, s.px, s.py, t3, s.tau, sample_index=n)
         assert np.array_equal(pairs, sorted_pairs(flat["pairs"]))
         assert np.array_equal(vis, hier["visits"].astype(np.uint32))
 

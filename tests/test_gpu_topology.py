@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import dev, run_cull, sorted_pairs, upload_scene
+from gpu_util import dev, oracle_hier, run_cull, sorted_pairs, upload_scene
 
 pytestmark = pytest.mark.gpu
 
@@ -91,10 +91,10 @@ def test_culling_over_cost_trees_is_exact(ctx):
     st, cnt, pairs, vis = run_cull(ctx, g, tree, float(s.tau), visits=True)
     assert st == 0
     t = oracle.Tree(s.light_pos, s.intensity, topology="cost")
-    hier = oracle.cull_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
+    hier = oracle_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau)
     assert np.array_equal(sorted_pairs(pairs), sorted_pairs(hier["pairs"]))
     assert np.array_equal(vis, hier["visits"].astype(np.uint32))
-    radix = oracle.cull_hier(oracle.Tree(s.light_pos, s.intensity), s.eye_pos, s.px, s.py, s.tile, s.tau)
+    radix = oracle_hier(oracle.Tree(s.light_pos, s.intensity), s.eye_pos, s.px, s.py, s.tile, s.tau)
     assert hier["total_visits"] < radix["total_visits"]
     # refit keeps the cost topology
     jit = (synth.uniform01(5, 1, 3 * len(s.light_pos)).reshape(-1, 3) - 0.5) * 0.05
