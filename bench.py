@@ -210,7 +210,8 @@ def run_ours(args):
     refit = run_refit(ctx, L, dev, stream) if ws == 1 else None
     # the step after the culling: weights and shadow segments of the accepted pairs
     connect = run_connect(ctx, E, L, tau, pairs, cnt, dev, stream) if ws == 1 else None
-    rangemin = run_rangemin(ctx, dev, stream, peaks) if ws == 1 and not args.no_rangemin else None
+    rangemin = (run_rangemin(ctx, dev, stream, peaks, n=args.rangemin_queries)
+                if ws == 1 and not args.no_rangemin else None)
     # several samples per light: psi(n) offsets and a space-time tile
     samples = run_samples(ctx, s, L, E, px, py, tau, pairs, stream) if ws == 1 else None
     del pairs, flush
@@ -223,15 +224,21 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             batched = run_batched(ctx, frames, stream, dev)
             if args.served_jobs > 0:
-                tn = {k: batched["tuning"][k] for k in ("rangemin_variant", "blocks_per_sm")}
-                served = {"config": run_served(ctx, frames, stream, dev, args.served_jobs, 200.0, tuning=tn)}
-                # the same at a load the GPU can sustain: 70% of its job-by-job capacity
+                import paper_1907_12343_gb300 as hrr_mod
+                tn = {k: batched["tuning"][k] for k in hrr_mod.TUNING_FIELDS}
+                # the GPU's job-by-job capacity on these frames (jobs/s); 200 jobs/s is several
+                # times that, so the configuration's own rate only measures queueing
                 cap_jobs = args.batch_frames / (batched["plain_job_by_job"]["ms"] / 1e3)
-                served["sustainable"] = run_served(ctx, frames, stream, dev, max(16, args.served_jobs // 4),
+                served = {"capacity_jobs_per_s": cap_jobs,
+                          "config": run_served(ctx, frames, stream, dev, args.served_jobs, 200.0, tuning=tn)}
+                served["config"]["offered_load"] = 200.0 / cap_jobs
+                # the same at a load the GPU can sustain: 70% of its job-by-job capacity, with
+                # enough jobs that p99 is a tail and not the maximum
+                served["sustainable"] = run_served(ctx, frames, stream, dev, args.sustained_jobs,
                                                    0.7 * cap_jobs, seed=12, tuning=tn)
                 # and with each job refitting its frame's hierarchy to moved lights first
-                served["sustainable_refit"] = run_served(ctx, frames, stream, dev, max(16, args.served_jobs // 4),
-                                                         0.7 * cap_jobs, seed=12, tuning=tn,
+                served["sustainable_refit"] = run_served(ctx, frames, stream, dev, max(16, args.served_jobs // 2),
+                                                         0.7 * cap_jobs, seed=13, tuning=tn,
                                                          refit_sets=moved_light_sets(frames, dev))
         for fr in frames:
             fr["tree"].free()
@@ -400,10 +407,10 @@ def other_fractions(V, accepted, n_e, n_l, sec, peaks, measured, tile_bytes):
 
 
 def run_e2e(ctx, s, dev, stream, args, cap):
-    """Same metric through the C ABI with host buffers: pinned host lights copied in and the
-    hierarchy built, then hrr_cull_host reads the eyes from pinned host memory and writes
-    the accepted pairs to pinned host memory (its slices' copies overlap the culling),
-    every step."""
+    """Same metric through the C ABI with host buffers, every step: hrr_build_light_tree_host
+    copies the lights from pinned host memory and builds the hierarchy, then hrr_cull_host
+    reads the eyes from pinned host memory and writes the accepted pairs to pinned host
+    memory (its slices' copies overlap the culling). Only the library moves data."""
     import numpy as np
     import torch
     import paper_1907_12343_gb300 as hrr
@@ -413,7 +420,6 @@ def run_e2e(ctx, s, dev, stream, args, cap):
     host_l.append(torch.from_numpy(s.intensity).pin_memory())
     host_e = [torch.from_numpy(np.ascontiguousarray(s.eye_pos[:, k])).pin_memory() for k in range(3)]
     host_e += [torch.from_numpy(s.px.view(np.int16)).pin_memory(), torch.from_numpy(s.py.view(np.int16)).pin_memory()]
-    dev_l = [torch.empty_like(h, device=dev) for h in host_l]
     host_pairs = torch.empty((cap, 2), dtype=torch.int32).pin_memory()
     h2d = sum(h.numel() * h.element_size() for h in host_l + host_e)
     steps = max(2, min(args.steps, 5))
@@ -422,9 +428,7 @@ def run_e2e(ctx, s, dev, stream, args, cap):
         for k in range(steps + 1):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            for h, d in zip(host_l, dev_l):
-                d.copy_(h, non_blocking=True)
-            tree = ctx.build_light_tree(*dev_l, topology=TOPOLOGY)
+            tree = ctx.build_light_tree_host(*host_l, topology=TOPOLOGY)
             st, cnt = ctx.cull_host(*host_e, tree, float(s.tau), host_pairs)
             tree.free()
             if st != hrr.HRR_OK:
@@ -534,7 +538,9 @@ def run_batched(ctx, frames, stream, dev, runs=3):
             "plain_job_by_job": {"value": total_pairs / t_p, "ms": t_p * 1e3},
             "speedup_vs_plain": t_p / t_b,
             "tuning": dict(tuning, size_class=cls, sample_eyes=min(big["n_e"], tuner.sample),
-                           sample_ms=entry["sample_ms"], tune_s=t_tune)}
+                           sample_ms=entry["sample_ms"], tune_s=t_tune,
+                           candidates=[dict(t, ms=round(ms, 3)) for t, ms in sorted(tuner.last_table,
+                                                                                    key=lambda tm: tm[1])])}
 
 
 def _latency_stats(lat):
@@ -651,11 +657,11 @@ def torch_stream(stream):
     return torch.cuda.stream(stream)
 
 
-def run_rangemin(ctx, dev, stream, peaks, n=1 << 24, reps=5):
-    """hrr_range_min over n seeded log-uniform (a, b, r) queries, the recipe of the 2^26-query
-    parity workload at 2^24 (335 MB of traffic, well above L2; generating 2^26 on the host
-    takes tens of seconds), inputs resident: median device time of reps launches, and its
-    HBM roofline (20 B per query: a, b, r read, minimum and argmin written)."""
+def run_rangemin(ctx, dev, stream, peaks, n=1 << 26, reps=5):
+    """hrr_range_min over the 2^26 seeded log-uniform (a, b, r) queries of the range-minimum
+    workload (1.34 GB of traffic, well above L2), inputs resident: median device time of reps
+    launches, and its HBM roofline (20 B per query: a, b, r read, minimum and argmin
+    written)."""
     import numpy as np
     import torch
     import synth
@@ -819,10 +825,34 @@ def _oracle_sample(s, n_sample):
     return ids
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(s, target_seconds=15.0):
     """Oracle hierarchical culling on the host cores over an evenly spaced eye sample,
-    scaled to a full frame: N_e N_l / (t_build + t_sample * N_e / n_sample)."""
+    scaled to a full frame: N_e N_l / (t_build + t_sample * N_e / n_sample); beside it the
+    same on one core (a smaller sample), and the flat brute force (every pair) on the
+    1024 x 4096 uniform workload."""
     import oracle
+    import synth
     n_e, n_l = len(s.eye_pos), len(s.light_pos)
     t0 = time.perf_counter()
     tree = oracle.Tree(s.light_pos, s.intensity, topology=TOPOLOGY)
@@ -835,10 +865,26 @@ def cpu_baseline(s, target_seconds=15.0):
             break
         n = min(n_e, int(n * max(2.0, target_seconds / max(res["seconds"], 1e-3))))
     t_full = t_build + res["seconds"] * n_e / n
+    # one core: a sample of about a quarter of the time budget
+    n1 = max(64, int(n * 0.25 * target_seconds / max(res["seconds"] * res["threads"], 1e-3)))
+    ids1 = _oracle_sample(s, min(n1, n_e))
+    r1 = oracle.cull_hier(tree, s.eye_pos[ids1], s.px[ids1], s.py[ids1], s.tile, s.tau, eye_ids=ids1, nthreads=1)
+    t1_full = t_build + r1["seconds"] * n_e / len(ids1)
+    # the flat brute force on the small uniform workload (4.2M pairs)
+    u = synth.scene_uniform()
+    tu = oracle.Tree(u.light_pos, u.intensity)
+    fl = oracle.cull_flat(tu, u.eye_pos, u.px, u.py, u.tile, u.tau)
+    pairs_u = len(u.eye_pos) * len(u.light_pos)
     return {"value": n_e * n_l / t_full, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+            "cpu_model": cpu_model(),
             "sample": f"oracle tree build over all {n_l} lights ({t_build:.2f} s) + hierarchical "
                       f"culling of {n} evenly spaced eyes ({res['seconds']:.2f} s), scaled to "
-                      f"{n_e} eyes"}
+                      f"{n_e} eyes",
+            "one_core": {"value": n_e * n_l / t1_full, "unit": UNIT, "cores": r1["threads"],
+                         "sample": f"{len(ids1)} evenly spaced eyes ({r1['seconds']:.2f} s) on one thread "
+                                   f"+ the build, scaled to {n_e} eyes"},
+            "flat_uniform_1024x4096": {"value": pairs_u / fl["seconds"], "unit": UNIT, "cores": fl["threads"],
+                                       "seconds": fl["seconds"], "accepted_pairs": int(len(fl["pairs"]))}}
 
 
 def frame_config(args, n_e, n_l, tau, height, ws):
@@ -902,8 +948,12 @@ def main(argv=None):
                     help="hierarchy shape over the Morton order (the same accepted set)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rangemin", action="store_true", help="skip the 2^26-query range-minimum leg")
+    ap.add_argument("--rangemin-queries", type=int, default=1 << 26, help="queries of the range-minimum leg")
     ap.add_argument("--batch-frames", type=int, default=64, help="0 skips the batched/served forms")
-    ap.add_argument("--served-jobs", type=int, default=256, help="0 skips the served form")
+    ap.add_argument("--served-jobs", type=int, default=256,
+                    help="jobs of the served run at the configuration's 200 jobs/s (0 skips the served form)")
+    ap.add_argument("--sustained-jobs", type=int, default=2000,
+                    help="jobs of the served run at 70%% of the GPU's job-by-job capacity")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     global TOPOLOGY

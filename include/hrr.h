@@ -192,6 +192,14 @@ typedef struct hrr_build_opts {
 int hrr_build_light_tree_ex(hrr_ctx *ctx, hrr_lights lights, uint32_t n_lights, const hrr_build_opts *opts,
                             hrr_tree **out);
 
+/* hrr_build_light_tree_ex with the lights in host memory (host SoA, n_lights entries each):
+ * the library copies them into a device staging area of the context (16 bytes a light,
+ * grown on demand, freed by hrr_destroy) on the context stream, then builds as
+ * hrr_build_light_tree_ex does. Pinned host memory lets the copies run at full bandwidth.
+ * Synchronous; statuses as hrr_build_light_tree_ex. */
+int hrr_build_light_tree_host(hrr_ctx *ctx, hrr_lights host_lights, uint32_t n_lights, const hrr_build_opts *opts,
+                              hrr_tree **out);
+
 /* Moved lights (the same lights, new positions and intensities; device SoA of the tree's
  * n lights, indexed by original light id): refit `tree` in place. The leaf order and the
  * topology of the build stay, so a light keeps its sequence index i (its position in the

@@ -168,7 +168,7 @@ def alg2_fixed(a: int, b: int, r: int, B: int = 32) -> int:
     return int(lib().or_alg2_fixed(a, b, r, B))
 
 
-METHODS = {"scan": 0, "trie": 1, "alg2": 2, "alg2_printed": 3, "alg1": 4}
+METHODS = {"scan": 0, "trie": 1, "alg2": 2, "alg2_printed": 3, "alg1": 4, "scan_inc": 5}
 
 
 def rangemin_batch(a, b, r, method: str = "trie", nthreads: int = 0, want_argmin: bool = True,

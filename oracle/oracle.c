@@ -99,6 +99,30 @@ uint32_t or_rangemin_scan(uint64_t a, uint64_t b, uint32_t r, int B, uint64_t *a
     return best;
 }
 
+/* The same scan over every index of [a,b) with 32-bit words, carrying the reversed index
+ * along instead of reversing each i from scratch: going from i - 1 to i flips the low
+ * ctz(i) + 1 binary digits of the index (its trailing ones and the zero above them), so
+ * the reversal flips the top ctz(i) + 1 digits. Used where every short range of a large
+ * query set is scanned. */
+uint32_t or_rangemin_scan_inc(uint64_t a, uint64_t b, uint32_t r, uint64_t *argmin)
+{
+    uint32_t rev = or_brev((uint32_t)a, 32);
+    uint32_t best = rev + r;
+    uint64_t best_i = a;
+    for (uint64_t i = a + 1; i < b; ++i) {
+        int t = __builtin_ctzll(i);
+        rev ^= 0xFFFFFFFFu << (31 - t);
+        uint32_t v = rev + r;
+        if (v < best) {
+            best = v;
+            best_i = i;
+        }
+    }
+    if (argmin)
+        *argmin = best_i;
+    return best;
+}
+
 /* Does some i in [a,b) end in the k binary digits p (i mod 2^k == p)? The first i >= a
  * with that ending is a + ((p - a) mod 2^k). */
 static int has_ending(uint64_t a, uint64_t b, uint64_t p, int k)
@@ -279,6 +303,9 @@ void or_rangemin_batch(const uint32_t *a, const uint32_t *b, const uint32_t *r, 
         case 1: v = or_rangemin_trie(a[q], b[q], r[q], B, &k); break;
         case 2: k = or_alg2_fixed(a[q], b[q], r[q], B); v = shifted_value(k, r[q], B); break;
         case 3: k = or_alg2_printed(a[q], b[q], r[q], B); v = shifted_value(k, r[q], B); break;
+        case 5:
+            v = B == 32 ? or_rangemin_scan_inc(a[q], b[q], r[q], &k) : or_rangemin_scan(a[q], b[q], r[q], B, &k);
+            break;
         default: k = or_alg1(a[q], b[q], B); v = shifted_value(k, 0, B); break;
         }
         vmin[q] = v;

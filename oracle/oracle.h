@@ -27,6 +27,9 @@ extern "C" {
 uint32_t or_brev(uint32_t x, int B);
 /* Linear scan: the definition of v(a,b) and its argmin (Sec. 1, Sec. 2). */
 uint32_t or_rangemin_scan(uint64_t a, uint64_t b, uint32_t r, int B, uint64_t *argmin);
+/* The scan with 32-bit words, the reversed index updated from one index to the next
+ * (brev(i) and brev(i - 1) differ in their top ctz(i) + 1 digits); a < b. */
+uint32_t or_rangemin_scan_inc(uint64_t a, uint64_t b, uint32_t r, uint64_t *argmin);
 /* Successor search in the binary trie of {brev(i) : i in [a,b)}: independent of Alg. 2. */
 uint32_t or_rangemin_trie(uint64_t a, uint64_t b, uint32_t r, int B, uint64_t *argmin);
 /* Alg. 1: the index in [a,b) with the most trailing zeros (the unshifted argmin). */
@@ -36,7 +39,7 @@ uint64_t or_alg2_printed(uint64_t a, uint64_t b, uint32_t r, int B);
 /* Alg. 2 with the a = 0 reading: fall back to Alg. 1 when the result is invalid. */
 uint64_t or_alg2_fixed(uint64_t a, uint64_t b, uint32_t r, int B);
 /* Batched range minimum with B-bit words (b <= 2^B - 1 when B = 32). method: 0 scan,
- * 1 trie, 2 Alg. 2 fixed, 3 Alg. 2 printed, 4 Alg. 1 (r ignored). The index returned by
+ * 1 trie, 2 Alg. 2 fixed, 3 Alg. 2 printed, 4 Alg. 1 (r ignored), 5 the incremental scan. The index returned by
  * methods 3 and 4 may lie outside [a,b) when the algorithm fails; its value is still
  * reported. argmin may be NULL. nthreads <= 0 uses every available thread. */
 void or_rangemin_batch(const uint32_t *a, const uint32_t *b, const uint32_t *r, uint64_t n,

@@ -147,6 +147,7 @@ _SIGS = {
     "hrr_set_shift_tile_3d": (_i32, [_P, _P, _u32, _u32, _u32]),
     "hrr_refit_light_tree": (_i32, [_P, _P, hrr_lights]),
     "hrr_build_light_tree_ex": (_i32, [_P, hrr_lights, _u32, C.POINTER(hrr_build_opts), C.POINTER(_P)]),
+    "hrr_build_light_tree_host": (_i32, [_P, hrr_lights, _u32, C.POINTER(hrr_build_opts), C.POINTER(_P)]),
     "hrr_build_scene": (_i32, [_P, _P, _u32, C.POINTER(_P)]),
     "hrr_free_scene": (_i32, [_P, _P]),
     "hrr_connect": (_i32, [_P, hrr_eyes, _u32, hrr_lights, _u32, _f32, _P, _u64, _P, _P, _P, _P]),
@@ -273,6 +274,16 @@ class Context:
         t = _P()
         opts = hrr_build_opts(TOPOLOGIES[topology], cost_depth)
         self.check(hrr_build_light_tree_ex(self.handle, L, n, C.byref(opts), C.byref(t)))
+        return Tree(self, t)
+
+    def build_light_tree_host(self, x, y, z, intensity, topology: str = "radix", cost_depth: int = 0) -> "Tree":
+        """build_light_tree from host arrays (numpy arrays or CPU tensors; pinned memory
+        copies fastest): the library stages them on the device itself."""
+        n = int(x.numel() if hasattr(x, "numel") else x.size)
+        L = hrr_lights(_ptr(x), _ptr(y), _ptr(z), _ptr(intensity))
+        t = _P()
+        opts = hrr_build_opts(TOPOLOGIES[topology], cost_depth)
+        self.check(hrr_build_light_tree_host(self.handle, L, n, C.byref(opts), C.byref(t)))
         return Tree(self, t)
 
     def refit_light_tree(self, tree: "Tree", x, y, z, intensity):

@@ -117,6 +117,7 @@ int hrr_destroy(hrr_ctx *ctx) {
     if (ctx->stream2) cudaStreamSynchronize(ctx->stream2);
     if (ctx->host_eyes_dev) cudaFree(ctx->host_eyes_dev);
     if (ctx->host_pairs_dev) cudaFree(ctx->host_pairs_dev);
+    if (ctx->host_lights_dev) cudaFree(ctx->host_lights_dev);
     if (ctx->slice_counters) cudaFree(ctx->slice_counters);
     if (ctx->sample_counters) cudaFree(ctx->sample_counters);
     if (ctx->ev_first) cudaEventDestroy(ctx->ev_first);
@@ -183,6 +184,37 @@ int hrr_build_light_tree_ex(hrr_ctx *ctx, hrr_lights lights, uint32_t n_lights, 
         return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "a light array is NULL");
     DeviceGuard g(ctx->device);
     return hrr_build_impl(ctx, lights, n_lights, out, topology, cost_depth);
+}
+
+int hrr_build_light_tree_host(hrr_ctx *ctx, hrr_lights H, uint32_t n_lights, const hrr_build_opts *opts,
+                              hrr_tree **out) {
+    if (!ctx) return HRR_ERR_INVALID_ARG;
+    if (!out) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_lights == 0 || n_lights > 0x7FFFFFFFu)
+        return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "n_lights must be in [1, 2^31 - 1]");
+    if (!H.x || !H.y || !H.z || !H.intensity) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "a light array is NULL");
+    DeviceGuard g(ctx->device);
+    const size_t stride = ((sizeof(float) * (size_t)n_lights + 255) & ~size_t(255)) / sizeof(float);
+    if (ctx->host_lights_cap < n_lights) {
+        HRR_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (ctx->host_lights_dev) cudaFree(ctx->host_lights_dev);
+        ctx->host_lights_dev = nullptr;
+        ctx->host_lights_cap = 0;
+        if (cudaMalloc(&ctx->host_lights_dev, 4 * sizeof(float) * stride) != cudaSuccess) {
+            cudaGetLastError();
+            return hrr_fail(ctx, HRR_ERR_OOM, "device staging area of the lights");
+        }
+        ctx->host_lights_cap = stride;
+    }
+    float *d = static_cast<float *>(ctx->host_lights_dev);
+    const size_t cap = ctx->host_lights_cap;  // floats per array in the staging area
+    const float *src[4] = {H.x, H.y, H.z, H.intensity};
+    for (int k = 0; k < 4; ++k)
+        HRR_CUDA(ctx, cudaMemcpyAsync(d + k * cap, src[k], sizeof(float) * (size_t)n_lights,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    const hrr_lights D{d, d + cap, d + 2 * cap, d + 3 * cap};
+    return hrr_build_light_tree_ex(ctx, D, n_lights, opts, out);
 }
 
 int hrr_free_light_tree(hrr_ctx *ctx, hrr_tree *tree) {

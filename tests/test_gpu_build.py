@@ -103,3 +103,26 @@ def test_nonfinite_lights_rejected(ctx, topology):
         with pytest.raises(hrr.HRRError) as e:
             ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"], topology=topology)
         assert e.value.status == hrr.HRR_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("topology", ["radix", "cost"])
+def test_build_from_host_lights_equals_device_build(ctx, topology):
+    # hrr_build_light_tree_host stages host lights itself; the hierarchy is the same
+    import torch
+    s = synth.scene_frame(width=8, height=8, n_lights=70001, tile_w=8, tile_h=8, seed=81)
+    g = upload_scene(s)
+    ref = ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"], topology=topology)
+    host = [torch.from_numpy(np.ascontiguousarray(s.light_pos[:, k])).pin_memory() for k in range(3)]
+    host.append(torch.from_numpy(np.ascontiguousarray(s.intensity)).pin_memory())
+    for _ in range(2):  # the staging area is reused
+        t = ctx.build_light_tree_host(*host, topology=topology)
+        a, pa = t.download()
+        b, pb = ref.download()
+        assert a.tobytes() == b.tobytes() and np.array_equal(pa, pb) and t.height == ref.height
+        t.free()
+    # pageable numpy arrays work too
+    t = ctx.build_light_tree_host(*[np.ascontiguousarray(s.light_pos[:, k]) for k in range(3)],
+                                  np.ascontiguousarray(s.intensity), topology=topology)
+    assert t.download()[0].tobytes() == ref.download()[0].tobytes()
+    t.free()
+    ref.free()

@@ -51,16 +51,22 @@ def test_all_short_ranges(ctx, variant):
 @pytest.mark.parametrize("variant", [0, 2])
 def test_log_uniform_queries_full_size(ctx, variant):
     # the 2^26-query range-minimum workload in the launch configuration used for timing:
-    # every query against the trie oracle, a sample of the short ones against the scan
+    # every query against the trie oracle; every query of at most 2^16 indices (about half
+    # of them, some 2 * 10^11 indices in all) against the scan over every index
     a, b, r = synth.rangemin_queries(1 << 26, seed=3)
     v, k = _run(ctx, a, b, r, variant)
     v_ref, k_ref = oracle.rangemin_batch(a, b, r, "trie")
     assert np.array_equal(v, v_ref)
     assert np.array_equal(k, k_ref)
     ln = b.astype(np.int64) - a.astype(np.int64)
-    idx = np.flatnonzero(ln <= 4096)[:400000]
+    idx = np.flatnonzero(ln <= 4096)[:100000]
     v_scan, k_scan = oracle.rangemin_batch(a[idx], b[idx], r[idx], "scan")
     assert np.array_equal(v[idx], v_scan) and np.array_equal(k[idx], k_scan)
+    if variant == 0:
+        idx = np.flatnonzero(ln <= 1 << 16)
+        assert len(idx) > (1 << 25) * 0.9
+        v_scan, k_scan = oracle.rangemin_batch(a[idx], b[idx], r[idx], "scan_inc")
+        assert np.array_equal(v[idx], v_scan) and np.array_equal(k[idx], k_scan)
 
 
 @pytest.mark.parametrize("variant", [0, 2])

@@ -215,3 +215,27 @@ def test_worked_example_bit_positions():
     assert (kp, kq) == (g["k_p"], g["k_q"])
     m = GOLDEN["left_to_right_mask"]
     assert m["k_r"] & ((2 << m["b_h"]) - 1) == m["m"]
+
+
+def test_incremental_scan_equals_scan():
+    # the scan that carries the reversed index along visits the same indices and values
+    aa, bb = np.triu_indices(513, k=1)
+    a = aa.astype(np.uint32)
+    b = bb.astype(np.uint32)
+    for r in (0, 1, 1 << 31, 0xFFFFFFFF, 0x9E3779B9):
+        rr = np.full(len(a), r, np.uint32)
+        v1, k1 = oracle.rangemin_batch(a, b, rr, "scan_inc")
+        v0, k0 = oracle.rangemin_batch(a, b, rr, "scan")
+        assert np.array_equal(v1, v0) and np.array_equal(k1, k0)
+    # random ranges of up to 5000 indices anywhere in [0, 2^32 - 1], including the top end
+    rng = np.random.default_rng(9)
+    n = 4000
+    ln = rng.integers(1, 5000, n).astype(np.uint64)
+    a = rng.integers(0, 2**32 - 5001, n).astype(np.uint64)
+    a[:50] = (2**32 - 1) - ln[:50]
+    a[50:100] = 0
+    b = a + ln
+    r = rng.integers(0, 2**32, n).astype(np.uint32)
+    v1, k1 = oracle.rangemin_batch(a.astype(np.uint32), b.astype(np.uint32), r, "scan_inc")
+    v0, k0 = oracle.rangemin_batch(a.astype(np.uint32), b.astype(np.uint32), r, "scan")
+    assert np.array_equal(v1, v0) and np.array_equal(k1, k0)
