@@ -62,7 +62,7 @@ def test_served_jobs_equal_the_oracle():
     moved = [mp[:, 0].contiguous(), mp[:, 1].contiguous(), mp[:, 2].contiguous(),
              torch.from_numpy(minten).to(dev())]
     # a space-time tile for scene 2's eyes
-    t3 = synth.shift_tile_3d(16, 16, 3, seed=62)
+    t3 = synth.shift_tile_3d(16, 16, 4, seed=62)
     t3_dev = _tile_dev(t3)
     # the frame-sized job
     big = synth.scene_frame()
@@ -87,7 +87,7 @@ def test_served_jobs_equal_the_oracle():
         if k % 2 == 1:
             time.sleep(0.003)  # later jobs arrive while earlier ones are on the GPU
     jobs.append((submit(g_r, tree_r, s_r["tau"], 0, len(s_r["eye_pos"]), tiles[1], refit=moved), "refit", None))
-    jobs.append((submit(gs[2], trees[2], small[2]["tau"], 0, 20000, t3_dev, sample_index=4), "spacetime", None))
+    jobs.append((submit(gs[2], trees[2], small[2]["tau"], 0, 20000, t3_dev, sample_index=5), "spacetime", None))
 
     for t, kind, info in jobs:
         r = srv.wait(t, 600.0)
@@ -108,9 +108,9 @@ def test_served_jobs_equal_the_oracle():
             assert np.array_equal(got, sorted_pairs(flat["pairs"]))
         elif kind == "spacetime":
             s = small[2]
-            to = oracle.Tree(s["light_pos"], s["intensity"])
+            to = oracle.Tree(s["light_pos"], s["intensity"], topology="cost")
             flat = oracle.cull_flat(to, s["eye_pos"][:20000], s["px"][:20000], s["py"][:20000], t3, s["tau"],
-                                    sample_index=4)
+                                    sample_index=5)
             assert np.array_equal(got, sorted_pairs(flat["pairs"]))
         else:
             ids = np.unique(np.concatenate([np.arange(0, n_big, n_big // 151), [n_big - 1]])).astype(np.uint32)
