@@ -1,11 +1,18 @@
-// Batched culling: many frames (each its own eyes, hierarchy, tile, tau and output) in one
-// persistent traversal launch (one per HRR_CULL_MAX_FRAMES frames), optionally recorded once
-// into a CUDA graph and replayed.
+// Batched culling: many frames (each its own eyes, hierarchy, tile, tau and output) culled
+// by a few persistent traversal launches, optionally recorded once into a CUDA graph and
+// replayed.
+//
+// A frame with enough eyes to fill the GPU by itself (kOwnLaunchEyes) gets a launch of its
+// own, which runs the single-frame kernel (its frame fields are kernel parameters in
+// registers); consecutive smaller frames share a batched launch of up to
+// HRR_CULL_MAX_FRAMES frames, whose warps look their frame up by eye. Launches alternate
+// between the context stream and a second stream of the batch, each with its own stack
+// spill area, so a launch's first blocks fill the SMs its predecessor's last eyes leave
+// idle; the second stream joins the context stream at the end.
 //
 // A batch keeps its frame descriptors on the host (they travel as kernel parameters) and its
 // per-frame counters, the launches' eye cursors and the device flags in device memory.
-// Replaying it resets the counters and runs the traversal over the eyes of every frame;
-// frames of very different sizes share a launch, so there is no per-frame launch overhead.
+// Replaying it resets the counters and runs every launch.
 #include <algorithm>
 #include <new>
 #include <vector>
@@ -24,7 +31,9 @@ struct hrr_batch {
     };
     std::vector<Part> parts;                    // one traversal launch each
     uint32_t spill_cap = 0;                     // stack spill entries per warp
-    void *spill = nullptr;                      // stack spill area (launches run in order)
+    void *spill[2] = {};                        // stack spill area per stream (two launches may overlap)
+    cudaStream_t side = nullptr;                // second stream (launches 1, 3, 5, ...)
+    cudaEvent_t fork = nullptr, join = nullptr; // side stream starts after the counter reset, ends before results
     unsigned long long *dev_counts = nullptr;  // 2 per frame (accepted, visits), a cursor per part, flags
     unsigned long long *host_counts = nullptr; // pinned mirror
     std::vector<uint64_t> caps;
@@ -38,15 +47,29 @@ struct hrr_batch {
 
 namespace {
 
+// Frames with at least this many eyes fill the GPU (152 SMs x 48 resident warps, one eye per
+// warp, several eyes per warp over a launch) and run as launches of their own.
+constexpr uint64_t kOwnLaunchEyes = 1u << 16;
+
 int enqueue(hrr_ctx *ctx, hrr_batch *b, cudaStream_t st) {
     HRR_CUDA(ctx, cudaMemsetAsync(b->dev_counts, 0, sizeof(unsigned long long) * b->n_counters(), st));
     unsigned long long *cursors = b->dev_counts + 2 * (size_t)b->n_frames;
     unsigned long long *flags = cursors + b->parts.size();
+    const bool two = b->parts.size() > 1;
+    if (two) {
+        HRR_CUDA(ctx, cudaEventRecord(b->fork, st));
+        HRR_CUDA(ctx, cudaStreamWaitEvent(b->side, b->fork, 0));
+    }
     for (size_t p = 0; p < b->parts.size(); ++p) {
         const hrr_batch::Part &pt = b->parts[p];
+        const int k = two ? (int)(p & 1) : 0;
         HRR_CUDA(ctx, hrr_cull_batch_enqueue(pt.grid, b->desc.data() + pt.first, pt.count, pt.total, cursors + p,
-                                             flags, b->spill, b->spill_cap, b->tuning, st));
+                                             flags, b->spill[k], b->spill_cap, b->tuning, k ? b->side : st));
         if (pt.total) ++ctx->launches;
+    }
+    if (two) {
+        HRR_CUDA(ctx, cudaEventRecord(b->join, b->side));
+        HRR_CUDA(ctx, cudaStreamWaitEvent(st, b->join, 0));
     }
     return HRR_OK;
 }
@@ -56,7 +79,11 @@ void release(hrr_batch *b) {
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
     if (b->dev_counts) cudaFree(b->dev_counts);
     if (b->host_counts) cudaFreeHost(b->host_counts);
-    if (b->spill) cudaFree(b->spill);
+    for (void *sp : b->spill)
+        if (sp) cudaFree(sp);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->side) cudaStreamDestroy(b->side);
     hrr_tile_release(b->ctx_tile, b->stream);
     delete b;
 }
@@ -105,7 +132,11 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
             release(b);
             return hrr_fail(ctx, status, bad);
         }
-        if (i % HRR_CULL_MAX_FRAMES == 0) {  // a new launch
+        // A new launch for a frame that fills the GPU, after one, or when the current
+        // shared launch is full (frames or eyes).
+        const bool big = fr.n_eyes >= kOwnLaunchEyes;
+        if (b->parts.empty() || big || b->parts.back().count == HRR_CULL_MAX_FRAMES ||
+            b->parts.back().total >= kOwnLaunchEyes) {
             b->parts.push_back(hrr_batch::Part{});
             b->parts.back().first = i;
             cursor = 0;
@@ -149,7 +180,12 @@ int hrr_batch_create(hrr_ctx *ctx, const hrr_frame *frames, uint32_t n_frames, c
         grid_max = std::max(grid_max, pt.grid);
     }
     b->spill_cap = hrr_cull_spill_cap(height, b->tuning.node_width);
-    cudaError_t e = cudaMalloc(&b->spill, hrr_cull_spill_entries(grid_max, height, b->tuning) * sizeof(uint2));
+    const size_t spill_bytes = hrr_cull_spill_entries(grid_max, height, b->tuning) * sizeof(uint2);
+    cudaError_t e = cudaMalloc(&b->spill[0], spill_bytes);
+    if (e == cudaSuccess && b->parts.size() > 1) e = cudaMalloc(&b->spill[1], spill_bytes);
+    if (e == cudaSuccess && b->parts.size() > 1) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&b->dev_counts, sizeof(unsigned long long) * b->n_counters());
     if (e == cudaSuccess) e = cudaMallocHost(&b->host_counts, sizeof(unsigned long long) * b->n_counters());
     if (e != cudaSuccess) {
