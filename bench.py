@@ -151,9 +151,11 @@ def run_ours(args):
     stream.synchronize()
     tau = float(s.tau)
 
+    form = {"node_width": args.node_width} if args.node_width else None
+
     def step():
         tree = ctx.build_light_tree(*L, topology=TOPOLOGY)
-        st, cnt = ctx.cull(*E, px, py, tree, tau, pairs)
+        st, cnt = ctx.cull(*E, px, py, tree, tau, pairs, tuning=form)
         tree.free()
         if st != hrr.HRR_OK:
             raise RuntimeError(f"cull status {st}")
@@ -203,6 +205,10 @@ def run_ours(args):
     measured = ctx.measure_peaks()  # L2, record-fetch and integer denominators (untimed)
     roof = roofline(V, cnt, n_e, cull_ms, peaks, kind, clk, workload=f"{args.eyes}x{n_l}", n_l=n_l,
                     measured=measured, tile_bytes=int(np.asarray(s.tile).nbytes))
+    if args.node_width == 4:
+        # the algorithmic op count per visit is that of binary visits: not comparable
+        roof.update(achieved=None, frac=None, ops_per_visit=None, node_width=4,
+                    note="visits are nodes of width four; the op-based roofline is defined for binary visits")
 
     # end to end through the public API with host buffers
     e2e = None if args.no_e2e else run_e2e(ctx, s, dev, stream, args, cap)
@@ -275,9 +281,11 @@ def run_ours(args):
 
 # Algorithmic work of one node visit on the frame workload with the cost-driven hierarchy
 # (counted with the oracle's traversal over 3,000 evenly spaced eyes): 1.960 internal child
-# tests x 27 float ops (bound + cull predicate) + 0.973 new range minima x 51 integer ops +
-# 0.988 inherited minima x 2 + 0.040 leaf tests x 17. The radix tree's mix gives 105.26.
-OPS_PER_VISIT = 1.960 * 27 + 0.973 * 51 + 0.988 * 2 + 0.040 * 17
+# tests x 21 ops (the box gap, 9; its square, 3 with fused multiply-adds; the distance floor
+# and the scaled bound, 4; the value of the range minimum, 2; the division-free cull
+# comparison, 3) + 0.973 new range minima x 51 integer ops + 0.988 inherited minima x 2 +
+# 0.040 leaf tests x 17.
+OPS_PER_VISIT = 1.960 * 21 + 0.973 * 51 + 0.988 * 2 + 0.040 * 17
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_1920x1080.md")
 TOPOLOGY = "cost"  # hierarchy shape of the benchmarked builds (set from --topology)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
@@ -946,6 +954,8 @@ def main(argv=None):
     ap.add_argument("--lights", type=int, default=1 << 20)
     ap.add_argument("--topology", choices=["cost", "radix"], default="cost",
                     help="hierarchy shape over the Morton order (the same accepted set)")
+    ap.add_argument("--node-width", type=int, choices=[0, 2, 4], default=0,
+                    help="traversal node width of the timed step (0: the library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rangemin", action="store_true", help="skip the 2^26-query range-minimum leg")
     ap.add_argument("--rangemin-queries", type=int, default=1 << 26, help="queries of the range-minimum leg")

@@ -95,6 +95,8 @@ def configure(L):
     L.or_rangemin_batch.argtypes = [P, P, P, u64, i32, i32, P, P, i32]
     L.or_fround.restype = f32
     L.or_fround.argtypes = [i32, f32, f32, i32]
+    L.or_fma_rd.restype = f32
+    L.or_fma_rd.argtypes = [f32, f32, f32]
     L.or_leaf_threshold.restype = u64
     L.or_leaf_threshold.argtypes = [f32, P, f32, P]
     L.or_node_culls.restype = i32
@@ -191,6 +193,11 @@ def fround(op: str, x: float, y: float, mode: int) -> np.float32:
     return np.float32(lib().or_fround(ops[op], np.float32(x), np.float32(y), mode))
 
 
+def fma_rd(x: float, y: float, z: float) -> np.float32:
+    """x y + z rounded once toward -inf, in float32."""
+    return np.float32(lib().or_fma_rd(np.float32(x), np.float32(y), np.float32(z)))
+
+
 def leaf_threshold(tau, l, intensity, e) -> int:
     l = np.ascontiguousarray(l, dtype=np.float32)
     e = np.ascontiguousarray(e, dtype=np.float32)
@@ -209,7 +216,9 @@ def node_cull_floor(tau, lo, hi, imax, e) -> int:
     test is monotone in v)."""
     if not node_culls(tau, lo, hi, imax, e, 0xFFFFFFFF):
         return 1 << 32
-    lo_v, hi_v = 0, 0xFFFFFFFF  # culls(hi_v) holds, culls(lo_v) does not (v = 0 never culls)
+    if node_culls(tau, lo, hi, imax, e, 0):
+        return 0
+    lo_v, hi_v = 0, 0xFFFFFFFF  # culls(hi_v) holds, culls(lo_v) does not
     while hi_v - lo_v > 1:
         mid = (lo_v + hi_v) // 2
         if node_culls(tau, lo, hi, imax, e, mid):

@@ -342,6 +342,29 @@ static float add_rd(float x, float y) { return or_fround(0, x, y, -1); }
 static float mul_rd(float x, float y) { return or_fround(2, x, y, -1); }
 static float mul_ru(float x, float y) { return or_fround(2, x, y, +1); }
 
+/* RD(x y + z) with one rounding, for finite floats. The product is exact in double (24 + 24
+ * significant bits); s = RN(x y + z) in double and its rounding error e are recovered
+ * exactly (two-sum). The float below x y + z is the float below s, unless s is itself a
+ * float and the exact sum lies below it (e < 0): then it is the next float down. (A float
+ * other than s cannot lie between s and s + e: both are doubles, |e| is at most half a
+ * double ulp of s.) */
+float or_fma_rd(float x, float y, float z)
+{
+    volatile double p = (double)x * (double)y;
+    volatile double sum = p + (double)z;
+    volatile double bb = sum - p;
+    volatile double e = (p - (sum - bb)) + ((double)z - bb);
+    int old = fegetround();
+    fesetround(FE_DOWNWARD);
+    volatile float f = (float)sum;
+    fesetround(old);
+    if ((double)f == sum && e < 0.0)
+        f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+static float fma_rd(float x, float y, float z) { return or_fma_rd(x, y, z); }
+
 /* ------------------------------------------------------------------------------------ */
 /* Acceptance thresholds                                                                  */
 /* ------------------------------------------------------------------------------------ */
@@ -390,34 +413,34 @@ static float u32_to_float_rd(uint32_t v)
 
 /* Can a node with box [lo,hi] and maximum intensity imax be culled when the minimum of the
  * eye's shifted sequence over its range is v? It can when v is at least the threshold of
- * every light inside. Per axis the gap to the box is max(0, RD(lo - e), RD(e - hi)),
- * squared and summed rounded down, floored at 1e-4: den_D <= the float32 max(d^2, 1e-4)
- * of any light in the box; num_U = RU(tau * max(imax, 0)) >= RN(tau * I) of any of them.
- * Each light's quotient is then at most num_U / den_D and its rounded value at most that
- * times (1 + 2^-24) (or below 2^-126, which needs only v >= 1). So the node is culled iff
- *     v >= 1  and  RD(RD(v) 2^-32 * den_D) >= RU(num_U (1 + 2^-23)) < +inf,
- * a division-free test: the left side is a lower bound of (v / 2^32) den_D and the right an
- * upper bound of num_U (1 + 2^-24). */
+ * every light inside. Per axis the gap to the box is max(0, RD(lo - e), RD(e - hi)); the
+ * squared gaps are summed with fused multiply-adds rounded down and floored at 1e-4:
+ * den_D <= the float32 max(d^2, 1e-4) of any light in the box. With the scale
+ * tau' = tau 2^32 (exact), num_U = RU(tau' max(imax, 0)) >= 2^32 RN(tau I) of any of them
+ * (when tau imax is a normal float), and each light's quotient RN(RN(tau I) / den) is at
+ * most its numerator over den_D times (1 + 2^-24). So the node is culled iff
+ *     RD(RD(v) den_D) >= RU(num_U (1 + 2^-23)),
+ * a division-free test whose left side is a lower bound of v den_D and right side an upper
+ * bound of 2^32 num (1 + 2^-24). Outside that chain it is sound too: v = 0 culls only when
+ * the right side is 0 (no light below has p > 0); if tau imax is subnormal every
+ * threshold is at most 1 and a cull needs v >= 1; an infinite right side never culls. */
 int or_node_culls(float tau, const float lo[3], const float hi[3], float imax, const float e[3],
                   uint32_t v)
 {
-    if (v == 0)
-        return 0;
-    float d2 = 0.0f;
+    float g[3];
     for (int k = 0; k < 3; ++k) {
         float below = sub_rd(lo[k], e[k]);
         float above = sub_rd(e[k], hi[k]);
-        float gap = fmaxf(0.0f, fmaxf(below, above));
-        float g2 = mul_rd(gap, gap);
-        d2 = (k == 0) ? g2 : add_rd(d2, g2);
+        g[k] = fmaxf(0.0f, fmaxf(below, above));
     }
+    float d2 = mul_rd(g[0], g[0]);
+    d2 = fma_rd(g[1], g[1], d2);
+    d2 = fma_rd(g[2], g[2], d2);
     float den = fmaxf(d2, kMinDist2);
-    float num = mul_ru(tau, fmaxf(imax, 0.0f));
+    float tau32 = tau * 4294967296.0f; /* exact: a power-of-two scaling */
+    float num = mul_ru(tau32, fmaxf(imax, 0.0f));
     float rhs = mul_ru(num, 1.00000012f); /* 1 + 2^-23 */
-    if (!(rhs < INFINITY))
-        return 0;
-    float w = u32_to_float_rd(v) * 2.3283064365386963e-10f; /* * 2^-32, exact */
-    float lhs = mul_rd(w, den);
+    float lhs = mul_rd(u32_to_float_rd(v), den);
     return lhs >= rhs;
 }
 

@@ -48,6 +48,8 @@ void or_rangemin_batch(const uint32_t *a, const uint32_t *b, const uint32_t *r, 
 /* ---- directed rounding primitives (exposed so tests can pin them) ---- */
 /* op: 0 add, 1 sub, 2 mul, 3 div; mode: -1 toward -inf, 0 nearest, +1 toward +inf */
 float or_fround(int op, float x, float y, int mode);
+/* x y + z rounded once toward -inf (a fused multiply-add rounded down). */
+float or_fma_rd(float x, float y, float z);
 
 /* ---- acceptance thresholds (float32, canonical operation order) ---- */
 /* t_ij = ceil(p_ij * 2^32), p_ij = min(1, (tau*I) / max(d^2, 1e-4)), round to nearest. */

@@ -179,6 +179,7 @@ __device__ __forceinline__ uint32_t range_argmin(uint32_t a, uint32_t b, uint32_
 // The eye a traversal works on.
 struct Eye {
     float x, y, z, tau;
+    float tau32;    // tau 2^32, the node test's scale
     uint32_t r, c;  // shift and brev(2^32 - r)
 };
 
@@ -194,7 +195,7 @@ struct Visit {
 // its range minimum at argmin k culls it; the box is (lo, imax, hi).
 __device__ __forceinline__ bool survives(const Eye &E, const float4 &lo, const float4 &hi, uint32_t k) {
     float den, rhs;
-    hrr_node_bound(E.tau, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w, E.x, E.y, E.z, den, rhs);
+    hrr_node_bound(E.tau32, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w, E.x, E.y, E.z, den, rhs);
     return !hrr_node_culls(__brev(k) + E.r, den, rhs);
 }
 
@@ -349,6 +350,7 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
         E.y = fr.ey[j];
         E.z = fr.ez[j];
         E.tau = fr.tau;
+        E.tau32 = fr.tau * 4294967296.0f;  // exact
         const uint32_t tx = fr.px[j] % fr.tile_w, ty = fr.py[j] % fr.tile_h;
         E.r = fr.tile[ty * fr.tile_w + tx] + fr.shift_offset;
         if (n_lights == 1) {  // the root is a leaf (record 0, slot 0, in either layout)

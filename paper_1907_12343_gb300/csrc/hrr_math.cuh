@@ -145,13 +145,20 @@ __device__ __forceinline__ float hrr_max3(float a, float b, float c) {
     return d;
 }
 
-// Conservative cull test of a node with box [lo, hi] and maximum intensity imax.
-// den = max(RD gap^2 sum, 1e-4) is at most the float32 max(d2, 1e-4) of any light in the
-// box; rhs = RU(RU(tau max(imax, 0)) (1 + 2^-23)) bounds num_i (1 + 2^-24) from above for
-// every light. The node is culled at range minimum v iff v >= 1, rhs < inf and
-// RD(RD(v) 2^-32 den) >= rhs: then v / 2^32 >= RN(num_i / den_i) for every light i, so v is
-// at least every leaf threshold (monotonicity of correctly rounded operations).
-__device__ __forceinline__ void hrr_node_bound(float tau, float lox, float loy, float loz,
+// Conservative cull test of a node with box [lo, hi] and maximum intensity imax, for an eye
+// at e, with the culling scale given as tau32 = tau 2^32 (exact: a power-of-two scaling).
+//   den = max(d2, 1e-4), d2 = RD(gz^2 + RD(gy^2 + RD(gx^2))) (fused, rounded down) with
+//         per-axis gaps g = max(0, RD(lo - e), RD(e - hi)): at most the float32 max(d^2, 1e-4)
+//         of any light in the box;
+//   rhs = RU(RU(tau32 max(imax, 0)) (1 + 2^-23)): at least 2^32 RN(tau I) (1 + 2^-23) of
+//         every light, when tau max(imax, 0) is a normal float.
+// The node is culled at range minimum v iff RD(RD(v) den) >= rhs. Then for every light i,
+// v den_i >= 2^32 RN(tau I_i) (1 + 2^-23) >= 2^32 RN(RN(tau I_i) / den_i), so v is at least
+// its threshold ceil(p_i 2^32). The cases outside that chain are sound as well: v = 0 culls
+// only when rhs = 0 (tau max(imax, 0) = 0: no light below has p > 0); if tau I is
+// subnormal every light's threshold is at most 1 and a cull needs v >= 1 (rhs > 0); an
+// infinite rhs never culls.
+__device__ __forceinline__ void hrr_node_bound(float tau32, float lox, float loy, float loz,
                                                float hix, float hiy, float hiz, float imax,
                                                float ex, float ey, float ez, float &den,
                                                float &rhs) {
@@ -159,14 +166,12 @@ __device__ __forceinline__ void hrr_node_bound(float tau, float lox, float loy, 
     const float gy = hrr_max3(0.0f, __fsub_rd(loy, ey), __fsub_rd(ey, hiy));
     const float gz = hrr_max3(0.0f, __fsub_rd(loz, ez), __fsub_rd(ez, hiz));
     float d2 = __fmul_rd(gx, gx);
-    d2 = __fadd_rd(d2, __fmul_rd(gy, gy));
-    d2 = __fadd_rd(d2, __fmul_rd(gz, gz));
+    d2 = __fmaf_rd(gy, gy, d2);
+    d2 = __fmaf_rd(gz, gz, d2);
     den = fmaxf(d2, 1e-4f);
-    rhs = __fmul_ru(__fmul_ru(tau, fmaxf(imax, 0.0f)), 1.00000012f);
+    rhs = __fmul_ru(__fmul_ru(tau32, fmaxf(imax, 0.0f)), 1.00000012f);
 }
 
 __device__ __forceinline__ bool hrr_node_culls(uint32_t v, float den, float rhs) {
-    if (v == 0u || !(rhs < __int_as_float(0x7f800000))) return false;
-    const float w = __fmul_rn(__uint2float_rd(v), 2.3283064365386963e-10f);  // exact * 2^-32
-    return __fmul_rd(w, den) >= rhs;
+    return __fmul_rd(__uint2float_rd(v), den) >= rhs;
 }

@@ -143,13 +143,36 @@ def test_node_cull_floor_of_single_light_is_tight():
             assert floor - leaf <= max(4, leaf * 2 ** -20)
 
 
+def test_fma_rd_brackets_exact_result():
+    # x y + z rounded once downward: the float at or below the exact rational value, and
+    # the next float up above it
+    rng = np.random.default_rng(11)
+    xs = (rng.standard_normal(4000) * 10.0 ** rng.integers(-6, 6, 4000)).astype(F)
+    ys = (rng.standard_normal(4000) * 10.0 ** rng.integers(-6, 6, 4000)).astype(F)
+    zs = (rng.standard_normal(4000) * 10.0 ** rng.integers(-12, 12, 4000)).astype(F)
+    zs[:500] = -(xs[:500].astype(np.float64) * ys[:500]).astype(F)  # near-cancellation
+    for x, y, z in zip(xs, ys, zs):
+        exact = Fraction(float(x)) * Fraction(float(y)) + Fraction(float(z))
+        f = oracle.fma_rd(x, y, z)
+        assert Fraction(float(f)) <= exact < Fraction(float(_ulp_up(f)))
+    # exact cases and one that rounds: 1 * 1 + 2^-30 rounds down to 1
+    assert oracle.fma_rd(3.0, 4.0, 5.0) == F(17.0)
+    assert oracle.fma_rd(1.0, 1.0, 2.0 ** -30) == F(1.0)
+    assert oracle.fma_rd(1.0, 1.0, -(2.0 ** -30)) == np.nextafter(F(1.0), F(0))
+
+
 def test_node_culls_zero_and_saturated():
     e = np.zeros(3, F)
     lo = np.array([1, 1, 1], F)
     hi = np.array([2, 2, 2], F)
-    # tau = 0: nothing below can be accepted; any positive minimum culls, v = 0 never does
-    assert oracle.node_cull_floor(F(0), lo, hi, F(5), e) == 1
-    assert not oracle.node_culls(F(0), lo, hi, F(5), e, 0)
+    # tau = 0 (or no positive intensity): no light below has p > 0, nothing can be accepted,
+    # so every minimum culls, v = 0 included
+    assert oracle.node_cull_floor(F(0), lo, hi, F(5), e) == 0
+    assert oracle.node_culls(F(0), lo, hi, F(5), e, 0)
+    assert oracle.node_culls(F(1e-3), lo, hi, F(-2), e, 0)
+    # any positive bound: v = 0 never culls (a light there may have threshold 1)
+    assert not oracle.node_culls(F(1e-30), lo, hi, F(1e-9), e, 0)
+    assert oracle.node_cull_floor(F(1e-30), lo, hi, F(1e-9), e) == 1
     # p saturates at 1: never culled
     assert oracle.node_cull_floor(F(1e30), lo, hi, F(5), e) == 1 << 32
     # eye inside the box with p = 1/2 at the distance floor: the floor is about 2^31
