@@ -287,6 +287,7 @@ def run_ours(args):
 # 0.040 leaf tests x 17.
 OPS_PER_VISIT = 1.960 * 21 + 0.973 * 51 + 0.988 * 2 + 0.040 * 17
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_1920x1080.md")
+PROFILE_SMALL = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_480x270.md")
 TOPOLOGY = "cost"  # hierarchy shape of the benchmarked builds (set from --topology)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", f)
                   for f in ("hrr_cull_kernel.cuh", "hrr_math.cuh")]
@@ -318,11 +319,11 @@ def build_source_hash() -> str:
     return kernel_source_hash([os.path.join(ROOT, "paper_1907_12343_gb300", "csrc", "hrr_build.cu")])
 
 
-def profiled_traffic(workload="", topology=None):
-    """DRAM bytes per cull launch from the committed ncu summary, if it was taken on the
-    current kernel source, on this workload and on this hierarchy shape (null otherwise)."""
+def _profile_keys(path, topology=None):
+    """The "- key: value" lines of a committed ncu summary, if it was taken on the current
+    kernel and build sources and on this hierarchy shape (None otherwise)."""
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(path).read()
     except OSError:
         return None
     vals = {}
@@ -332,14 +333,35 @@ def profiled_traffic(workload="", topology=None):
             vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
     if vals.get("kernel_source_sha256") != kernel_source_hash():
         return None
-    if workload and vals.get("workload_eyes") != workload:
-        return None
     if vals.get("topology") != (topology or TOPOLOGY):
         return None
     if vals.get("build_source_sha256") != build_source_hash():
         return None
+    return vals
+
+
+def profiled_traffic(workload="", topology=None):
+    """DRAM bytes per cull launch from the committed ncu summary, if it was taken on the
+    current kernel source, on this workload and on this hierarchy shape (null otherwise)."""
+    vals = _profile_keys(PROFILE_SUMMARY, topology)
+    if not vals or (workload and vals.get("workload_eyes") != workload):
+        return None
     try:
         return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def profiled_l2(topology=None):
+    """L2 throughput of the cull kernel from the committed small-frame ncu summary (bytes/s
+    through the L2 slices and their busy fraction), if taken on the current sources."""
+    vals = _profile_keys(PROFILE_SMALL, topology)
+    if not vals:
+        return None
+    try:
+        return {"workload": vals["workload_eyes"], "l2_bytes_per_s": float(vals["l2_bytes_per_s"]),
+                "l2_throughput_pct": float(vals["l2_throughput_pct"]),
+                "l1_throughput_pct": float(vals["l1_throughput_pct"])}
     except (KeyError, ValueError):
         return None
 
@@ -407,6 +429,11 @@ def other_fractions(V, accepted, n_e, n_l, sec, peaks, measured, tile_bytes):
         unique = 64.0 * max(n_l - 1, 1) + 16.0 * n_e + tile_bytes + 8.0 * accepted
         out["hbm"] = {"unique_bytes": unique, "achieved_gbs": unique / sec / 1e9, "peak_gbs": peaks["hbm_gbs"],
                       "frac": unique / sec / 1e9 / peaks["hbm_gbs"]}
+    l2 = profiled_l2()
+    if l2 and measured.get("l2_read_gbs"):
+        # the L2 traffic ncu counts on the small frame (every sector the L2 serves: records,
+        # stack spills, output), against the measured L2 streaming read
+        out["l2_ncu"] = dict(l2, frac_of_l2_stream=l2["l2_bytes_per_s"] / 1e9 / measured["l2_read_gbs"])
     if measured.get("int_ops_per_s"):
         ach = V * OPS_PER_VISIT / sec
         out["int32"] = {"achieved_per_s": ach, "peak_per_s": measured["int_ops_per_s"],

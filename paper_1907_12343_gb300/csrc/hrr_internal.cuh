@@ -146,7 +146,7 @@ struct hrr_cull_frame_t {
 // Traversal defaults: node width, shared-memory stack ring per warp, threads per block.
 #define HRR_DEFAULT_NODE_WIDTH 2u
 #define HRR_DEFAULT_RING 256u
-#define HRR_DEFAULT_THREADS 256u
+#define HRR_DEFAULT_THREADS 128u
 
 // Launch parameters with the library defaults filled in.
 inline hrr_tuning hrr_tuning_normalized(hrr_tuning t) {
