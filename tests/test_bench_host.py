@@ -52,3 +52,10 @@ def test_both_arms_describe_the_same_workload(bench):
     a = bench.frame_config(args, 2073600, 1048576, 3e-6, 30, 1)
     assert a["topology"] == bench.TOPOLOGY and a["n_eyes"] == 2073600 and a["parallelism"] == "replicas x1"
     assert set(a) >= {"workload", "n_eyes", "n_lights", "tau", "tree_height", "step", "topology", "l2"}
+
+
+def test_l2_figures_come_from_the_small_frame_profile(bench):
+    l2 = bench.profiled_l2()
+    assert l2 is None or (l2["workload"] == "480x270x1048576" and l2["l2_bytes_per_s"] > 1e12
+                          and 0 < l2["l2_throughput_pct"] <= 100)
+    assert bench.profiled_l2(topology="radix") is None
