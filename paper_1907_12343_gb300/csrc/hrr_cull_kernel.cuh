@@ -1,4 +1,4 @@
-// The culling traversal kernels and their launch helpers; hrr_cull.cu holds the host entry points.
+// The culling traversal kernels (device code only); hrr_cull.cu instantiates and launches them.
 //
 // Hierarchical Russian-roulette culling with blue-noise dithered QMC sequences (Sec. 1).
 //
@@ -44,7 +44,6 @@
 #pragma once
 
 #include <algorithm>
-#include <vector>
 
 #include "hrr_internal.cuh"
 
@@ -464,83 +463,6 @@ template <int VARIANT, int W, int RING, int THREADS>
 __global__ void __launch_bounds__(THREADS, min_blocks<W>(THREADS))
 cull_batch_kernel(const __grid_constant__ Launch Lc, const __grid_constant__ FrameArray<kMaxFrames> FA) {
     traverse<VARIANT, true, W, RING, THREADS>(Lc, FA.f);
-}
-
-// ------------------------------------------------------------------------------------
-// Instantiations and their dispatch
-// ------------------------------------------------------------------------------------
-
-// One compiled form of the traversal: range-minimum variant, node width, ring entries per
-// warp and threads per block, with its single-frame and batched kernels.
-struct CullKernel {
-    int variant, width, ring, threads;
-    const void *single, *batch;
-    int occ[2];  // resident blocks per SM (single, batched), 0 until first asked
-};
-
-template <int VARIANT, int W, int RING, int THREADS>
-CullKernel cull_entry() {
-    return {VARIANT, W, RING, THREADS, reinterpret_cast<const void *>(cull_single_kernel<VARIANT, W, RING, THREADS>),
-            reinterpret_cast<const void *>(cull_batch_kernel<VARIANT, W, RING, THREADS>), {0, 0}};
-}
-
-template <int VARIANT>
-void add_entries(std::vector<CullKernel> &v) {
-    v.push_back(cull_entry<VARIANT, 2, 256, 256>());
-    v.push_back(cull_entry<VARIANT, 2, 128, 256>());
-    v.push_back(cull_entry<VARIANT, 2, 256, 128>());
-    v.push_back(cull_entry<VARIANT, 2, 128, 128>());
-    v.push_back(cull_entry<VARIANT, 4, 256, 256>());
-    v.push_back(cull_entry<VARIANT, 4, 512, 256>());
-    v.push_back(cull_entry<VARIANT, 4, 256, 128>());
-    v.push_back(cull_entry<VARIANT, 4, 512, 128>());
-}
-
-std::vector<CullKernel> &cull_kernels() {
-    static std::vector<CullKernel> v = [] {
-        std::vector<CullKernel> t;
-        add_entries<0>(t);
-        add_entries<2>(t);
-        return t;
-    }();
-    return v;
-}
-
-// The compiled form for a normalised tuning (nullptr if there is none).
-CullKernel *cull_kernel_for(const hrr_tuning &t) {
-    for (CullKernel &k : cull_kernels())
-        if (k.variant == t.rangemin_variant && k.width == (int)t.node_width && k.ring == (int)t.ring_entries &&
-            k.threads == (int)t.threads_per_block)
-            return &k;
-    return nullptr;
-}
-
-int cull_occupancy(CullKernel &k, bool batch) {
-    int &n = k.occ[batch ? 1 : 0];
-    if (!n) {
-        int m = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, batch ? k.batch : k.single, k.threads, 0) !=
-                cudaSuccess || m < 1) {
-            cudaGetLastError();
-            m = 1;
-        }
-        n = m;
-    }
-    return n;
-}
-
-cudaError_t launch_single(CullKernel &k, unsigned grid, const Launch &Lc, const Frame &fr, cudaStream_t st) {
-    Launch lc = Lc;
-    Frame f = fr;
-    void *args[] = {&lc, &f};
-    return cudaLaunchKernel(k.single, dim3(grid), dim3(k.threads), args, 0, st);
-}
-
-cudaError_t launch_batch(CullKernel &k, unsigned grid, const Launch &Lc, const FrameArray<kMaxFrames> &fa,
-                         cudaStream_t st) {
-    Launch lc = Lc;
-    void *args[] = {&lc, const_cast<FrameArray<kMaxFrames> *>(&fa)};
-    return cudaLaunchKernel(k.batch, dim3(grid), dim3(k.threads), args, 0, st);
 }
 
 }  // namespace
