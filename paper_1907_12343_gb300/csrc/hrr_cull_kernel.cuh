@@ -422,11 +422,15 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
                     R -= s;
                     __syncwarp();
                 }
+                // Lane by lane, each lane's survivors side by side: siblings (whose records
+                // are neighbours in memory) are popped together by neighbouring lanes.
                 uint32_t pos = S;
 #pragma unroll
+                for (int t = 0; t < W; ++t) pos += __popc(bal[t] & lt);
+#pragma unroll
                 for (int t = 0; t < W; ++t) {
-                    if (V.go[t]) ring[(pos + __popc(bal[t] & lt)) & kRingMask] = make_uint2(V.node[t], V.karg[t]);
-                    pos += __popc(bal[t]);
+                    if (V.go[t]) ring[pos & kRingMask] = make_uint2(V.node[t], V.karg[t]);
+                    pos += V.go[t] ? 1u : 0u;
                 }
                 S += n;
                 R += n;
