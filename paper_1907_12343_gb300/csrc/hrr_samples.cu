@@ -235,8 +235,11 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cull_samples_kernel(cons
                     R -= sp;
                     __syncwarp();
                 }
-                if (go0) ring[(S + __popc(b0 & lt)) & kRingMask] = make_uint2(split, mask0);
-                if (go1) ring[(S + __popc(b0) + __popc(b1 & lt)) & kRingMask] = make_uint2(split + 1u, mask1);
+                // lane by lane, siblings side by side (popped together by neighbouring lanes,
+                // whose records are neighbours in memory)
+                const uint32_t at = S + __popc(b0 & lt) + __popc(b1 & lt);
+                if (go0) ring[at & kRingMask] = make_uint2(split, mask0);
+                if (go1) ring[(at + (go0 ? 1u : 0u)) & kRingMask] = make_uint2(split + 1u, mask1);
                 S += n;
                 R += n;
                 __syncwarp();
