@@ -201,3 +201,33 @@ def test_new_context_tile_leaves_batch_and_job_on_their_tile(ctx):
     assert st2 == hrr.HRR_OK
     assert not np.array_equal(sorted_pairs(pairs2), sorted_pairs(ref))
     fr["tree"].free()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_mixed_batch_own_and_shared_launches(ctx, use_graph):
+    # frames with at least 2^16 eyes run as launches of their own (the single-frame kernel,
+    # alternating streams), the small ones between them share batched launches; every frame
+    # gets exactly its plain result, on replays too
+    import paper_1907_12343_gb300 as hrr
+    big_a = dict(synth.scene_frame(width=256, height=256, n_lights=20011, tile_w=64, tile_h=64,
+                                   target=32.0, seed=61))
+    big_b = dict(synth.scene_frame(width=320, height=240, n_lights=7001, tile_w=16, tile_h=16,
+                                   target=16.0, seed=62))
+    smalls = _scenes()[:3]
+    order = [big_a, smalls[0], smalls[1], big_b, smalls[2], big_a]
+    frames = [_frame(ctx, s, cap=max(1024, 160 * len(s["eye_pos"]))) for s in order]
+    b = hrr.Batch(ctx, frames, use_graph=use_graph)
+    for rep in range(2):
+        b.launch()
+        st, counts, visits = b.results()
+        assert st == hrr.HRR_OK
+        for fr, cnt, v in zip(frames, counts, visits):
+            got = fr["pairs"][:cnt].cpu().numpy().view(np.uint32)
+            if rep == 0:
+                pst, ref, ref_vis = _plain(ctx, fr)
+                fr["_ref"] = (sorted_pairs(ref), int(ref_vis.sum()))
+            assert np.array_equal(sorted_pairs(got), fr["_ref"][0])
+            assert v == fr["_ref"][1]
+    b.destroy()
+    for fr in frames:
+        fr["tree"].free()
