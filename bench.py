@@ -151,7 +151,7 @@ def run_ours(args):
     stream.synchronize()
     tau = float(s.tau)
 
-    form = {"node_width": args.node_width} if args.node_width else None
+    form = {k: v for k, v in (("node_width", args.node_width), ("top_levels", args.top_levels)) if v} or None
 
     def step():
         tree = ctx.build_light_tree(*L, topology=TOPOLOGY)
@@ -983,6 +983,8 @@ def main(argv=None):
                     help="hierarchy shape over the Morton order (the same accepted set)")
     ap.add_argument("--node-width", type=int, choices=[0, 2, 4], default=0,
                     help="traversal node width of the timed step (0: the library default)")
+    ap.add_argument("--top-levels", type=int, choices=[0, 1, 6], default=0,
+                    help="top levels the traversal evaluates from shared memory (1: none, 0: the library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-rangemin", action="store_true", help="skip the 2^26-query range-minimum leg")
     ap.add_argument("--rangemin-queries", type=int, default=1 << 26, help="queries of the range-minimum leg")

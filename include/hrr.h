@@ -115,15 +115,23 @@ typedef struct hrr_cull_opts {
      * 0 for a plain tile */
     uint32_t sample_index;
     /* traversal form (results do not depend on it; 0 = the library default for each, see
-     * hrr_default_tuning: width 2, 256 ring entries, 128 threads):
+     * hrr_default_tuning: width 2, 256 ring entries, 128 threads, 6 top levels):
      *   node_width: 2 = binary records (a visit tests both children), 4 = the hierarchy read
      *     with nodes of width four (a visit tests the four grandchildren);
      *   ring_entries: stack entries per warp kept in shared memory, 128 or 256 for width 2,
      *     256 or 512 for width 4;
-     *   threads_per_block: 128 or 256 (one eye per warp). */
+     *   threads_per_block: 128 or 256 (one eye per warp);
+     *   top_levels: 1 = every level is walked from the root; 6 (width 2 only) = each block
+     *     stages the top six levels of the hierarchy (63 nodes) in shared memory, and each
+     *     eye first evaluates the 62 nodes below the root there in two warp-wide passes.
+     *     The cull test is monotone (a child's smaller box, smaller maximum intensity and
+     *     larger range minimum never turn its parent's cull into a visit), so a node below
+     *     the root is visited iff its own test passes, and those levels need not be walked
+     *     one level per step. Batched launches of several frames walk from the root. */
     uint32_t node_width;
     uint32_t ring_entries;
     uint32_t threads_per_block;
+    uint32_t top_levels;
 } hrr_cull_opts;
 
 /* Launch parameters of the traversal (see hrr_cull_opts); none changes any result. Zero
@@ -134,10 +142,11 @@ typedef struct hrr_tuning {
     uint32_t node_width;
     uint32_t ring_entries;
     uint32_t threads_per_block;
+    uint32_t top_levels;
 } hrr_tuning;
 
 /* The tuning the library uses for zero fields (rangemin_variant 0, blocks_per_sm 0 = as many
- * as fit, and the default node width, ring size and threads per block). */
+ * as fit, and the default node width, ring size, threads per block and top levels). */
 int hrr_default_tuning(hrr_tuning *out);
 
 /* ---- context --------------------------------------------------------------------------- */

@@ -88,7 +88,8 @@ class hrr_cull_opts(C.Structure):
     _fields_ = [("eye_visits", C.c_void_p), ("rangemin_variant", C.c_int),
                 ("shift_offset", C.c_uint32), ("blocks_per_sm", C.c_uint32),
                 ("sample_index", C.c_uint32), ("node_width", C.c_uint32),
-                ("ring_entries", C.c_uint32), ("threads_per_block", C.c_uint32)]
+                ("ring_entries", C.c_uint32), ("threads_per_block", C.c_uint32),
+                ("top_levels", C.c_uint32)]
 
 
 class hrr_peaks(C.Structure):
@@ -103,12 +104,13 @@ HRR_TOPOLOGY_RADIX, HRR_TOPOLOGY_COST = 0, 1
 TOPOLOGIES = {"radix": HRR_TOPOLOGY_RADIX, "cost": HRR_TOPOLOGY_COST}
 
 
-TUNING_FIELDS = ("rangemin_variant", "blocks_per_sm", "node_width", "ring_entries", "threads_per_block")
+TUNING_FIELDS = ("rangemin_variant", "blocks_per_sm", "node_width", "ring_entries", "threads_per_block",
+                 "top_levels")
 
 
 class hrr_tuning(C.Structure):
     _fields_ = [("rangemin_variant", C.c_int), ("blocks_per_sm", C.c_uint32), ("node_width", C.c_uint32),
-                ("ring_entries", C.c_uint32), ("threads_per_block", C.c_uint32)]
+                ("ring_entries", C.c_uint32), ("threads_per_block", C.c_uint32), ("top_levels", C.c_uint32)]
 
     @classmethod
     def from_dict(cls, d):
@@ -125,7 +127,8 @@ def _opts(eye_visits, tuning, rangemin_variant, shift_offset, sample_index):
     t = tuning or {}
     return hrr_cull_opts(_ptr(eye_visits), int(t.get("rangemin_variant", rangemin_variant)), int(shift_offset),
                          int(t.get("blocks_per_sm", 0)), int(sample_index), int(t.get("node_width", 0)),
-                         int(t.get("ring_entries", 0)), int(t.get("threads_per_block", 0)))
+                         int(t.get("ring_entries", 0)), int(t.get("threads_per_block", 0)),
+                         int(t.get("top_levels", 0)))
 
 
 _P = C.c_void_p

@@ -268,7 +268,7 @@ int hrr_refit_light_tree(hrr_ctx *ctx, hrr_tree *tree, hrr_lights lights) {
     void *scratch = nullptr;
     HRR_CUDA(ctx, cudaMallocAsync(&scratch, hrr_refit_scratch_bytes(tree->n), st));
     const cudaError_t e = hrr_refit_enqueue(tree, lights, scratch, flags, st);
-    ctx->launches += tree->n > 1 ? 4 : 2;
+    ctx->launches += hrr_refit_launches(tree);
     cudaFreeAsync(scratch, st);
     HRR_CUDA(ctx, e);
     HRR_CUDA(ctx, cudaMemcpyAsync(&ctx->host_counters[2], flags, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));

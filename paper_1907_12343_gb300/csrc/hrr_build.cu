@@ -317,6 +317,56 @@ __global__ void single_leaf_kernel(const float *x, const float *y, const float *
     perm[0] = 0;
 }
 
+// The top slots (HRR_TOP_SLOTS of them, layout in hrr_internal.cuh): thread s walks from the
+// root along the path of heap slot s (the bits of s + 1 below its leading one, high to low:
+// 0 = child 0, 1 = child 1), taking each child's box and maximum intensity from its parent's
+// record. A slot below a leaf is empty; a record whose split is outside its node's range
+// (not produced by the builder) empties the slots below it.
+__global__ void __launch_bounds__(64) top_kernel(const float4 *__restrict__ nodes, uint32_t n,
+                                                 float4 *__restrict__ top, const unsigned long long *flags) {
+    const uint32_t s = threadIdx.x;
+    if (s >= HRR_TOP_SLOTS) return;
+    if (*(volatile const unsigned long long *)flags & HRR_FLAG_NONFINITE) return;
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    uint32_t first = 0, last = 0, node = 0, kind = HRR_TOP_EMPTY;
+    if (n > 1) {
+        const uint32_t path = s + 1u;
+        kind = HRR_TOP_INTERNAL;
+        last = __float_as_uint(nodes[3].w);  // the root's range is [0, its other end]
+        for (int b = 30 - __clz(path); b >= 0; --b) {
+            if (kind != HRR_TOP_INTERNAL) {
+                kind = HRR_TOP_EMPTY;
+                break;
+            }
+            const float4 *r = nodes + 4 * (size_t)node;
+            const uint32_t split = __float_as_uint(r[1].w);
+            if (last >= n || split < first || split >= last) {
+                kind = HRR_TOP_EMPTY;
+                break;
+            }
+            if (((path >> b) & 1u) == 0u) {
+                lo = r[0];
+                hi = r[1];
+                last = split;
+                node = split;
+            } else {
+                lo = r[2];
+                hi = r[3];
+                first = split + 1u;
+                node = split + 1u;
+            }
+            kind = first == last ? HRR_TOP_LEAF : HRR_TOP_INTERNAL;
+        }
+    }
+    if (kind == HRR_TOP_EMPTY) {
+        lo = hi = make_float4(0.f, 0.f, 0.f, 0.f);
+        first = last = node = 0;
+    }
+    top[3 * s] = lo;
+    top[3 * s + 1] = make_float4(hi.x, hi.y, hi.z, __uint_as_float(first));
+    top[3 * s + 2] = make_float4(__uint_as_float(last), __uint_as_float(node), __uint_as_float(kind), 0.f);
+}
+
 // Records of width four. The record of internal node g holds, in this order, the slots of
 // g's grandchildren over its leaf range [first, last] split at `split`:
 //   slot 0: [first, s0]      slot 1: [s0 + 1, split]     (the children of child 0)
@@ -972,7 +1022,7 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
         return status;
     };
     const uint32_t n_rec = n > 1 ? n - 1 : 1;
-    cudaError_t e = cudaMallocAsync(&tree->nodes, sizeof(hrr_node) * (size_t)n_rec, st);
+    cudaError_t e = cudaMallocAsync(&tree->nodes, sizeof(hrr_node) * (size_t)n_rec + HRR_TOP_BYTES, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&tree->perm, sizeof(uint32_t) * (size_t)n, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&tree->wide, 8 * sizeof(float4) * (size_t)n_rec, st);
     if (e != cudaSuccess) return fail(hrr_cuda_fail(ctx, e, "tree allocation"));
@@ -1045,8 +1095,9 @@ int hrr_build_impl(hrr_ctx *ctx, const hrr_lights &L, uint32_t n, hrr_tree **out
         cudaFreeAsync(scratch, st);
         if (rc != HRR_OK) return fail(rc);
     }
-    if ((e = hrr_widen_enqueue(tree, flags, st)) != cudaSuccess) return fail(hrr_cuda_fail(ctx, e, "widen_kernel"));
-    ++ctx->launches;
+    if ((e = hrr_derived_enqueue(tree, flags, st)) != cudaSuccess)
+        return fail(hrr_cuda_fail(ctx, e, "top and widen kernels"));
+    ctx->launches += hrr_derived_launches(tree);
     if ((e = cudaMemcpyAsync(&ctx->host_counters[2], flags, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return fail(hrr_cuda_fail(ctx, e, "flag copy"));
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return fail(hrr_cuda_fail(ctx, e, "build"));
@@ -1077,7 +1128,7 @@ cudaError_t hrr_refit_enqueue(hrr_tree *tree, const hrr_lights &L, void *scratch
         // one leaf: rewrite the single record unless the light is not finite (checked there)
         single_leaf_kernel<<<1, 1, 0, st>>>(L.x, L.y, L.z, L.intensity, tree->nodes, tree->perm, flags);
         const cudaError_t e = cudaGetLastError();
-        return e == cudaSuccess ? hrr_widen_enqueue(tree, flags, st) : e;
+        return e == cudaSuccess ? hrr_derived_enqueue(tree, flags, st) : e;
     }
     char *p = static_cast<char *>(scratch_mem);
     float4 *spos = carve<float4>(p, n);
@@ -1095,14 +1146,17 @@ cudaError_t hrr_refit_enqueue(hrr_tree *tree, const hrr_lights &L, void *scratch
     refit_kernel<<<g, kThreads, 0, st>>>(spos, n, tree->nodes, leaf_parent, int_parent, arrivals, child_height,
                                          root_height, flags);
     e = cudaGetLastError();
-    return e == cudaSuccess ? hrr_widen_enqueue(tree, flags, st) : e;
+    return e == cudaSuccess ? hrr_derived_enqueue(tree, flags, st) : e;
 }
 
-cudaError_t hrr_widen_enqueue(hrr_tree *tree, const unsigned long long *flags, cudaStream_t st) {
-    if (!tree->wide) return cudaSuccess;
+cudaError_t hrr_derived_enqueue(hrr_tree *tree, const unsigned long long *flags, cudaStream_t st) {
     const uint32_t n = tree->n;
+    const float4 *nodes = reinterpret_cast<const float4 *>(tree->nodes);
+    const size_t n_rec = n > 1 ? n - 1 : 1;
+    top_kernel<<<1, 64, 0, st>>>(nodes, n, reinterpret_cast<float4 *>(tree->nodes) + 4 * n_rec, flags);
+    if (!tree->wide) return cudaGetLastError();
     const unsigned g = n > 1 ? (n - 1 + kThreads - 1) / kThreads : 1;
-    widen_kernel<<<g, kThreads, 0, st>>>(reinterpret_cast<const float4 *>(tree->nodes), n, tree->wide, flags);
+    widen_kernel<<<g, kThreads, 0, st>>>(nodes, n, tree->wide, flags);
     return cudaGetLastError();
 }
 

@@ -13,29 +13,37 @@ namespace {
 // ------------------------------------------------------------------------------------
 
 // One compiled form of the traversal: range-minimum variant, node width, ring entries per
-// warp and threads per block, with its single-frame and batched kernels.
+// warp, threads per block and top levels evaluated by the head, with its single-frame and
+// batched kernels (batched launches of several frames walk from the root: a form with top
+// levels shares the batched kernel of its form without them).
 struct CullKernel {
-    int variant, width, ring, threads;
+    int variant, width, ring, threads, top;
     const void *single, *batch;
     int occ[2];  // resident blocks per SM (single, batched), 0 until first asked
 };
 
-template <int VARIANT, int W, int RING, int THREADS>
+template <int VARIANT, int W, int RING, int THREADS, int TOP>
 CullKernel cull_entry() {
-    return {VARIANT, W, RING, THREADS, reinterpret_cast<const void *>(cull_single_kernel<VARIANT, W, RING, THREADS>),
+    return {VARIANT, W, RING, THREADS, TOP,
+            reinterpret_cast<const void *>(cull_single_kernel<VARIANT, W, RING, THREADS, TOP>),
             reinterpret_cast<const void *>(cull_batch_kernel<VARIANT, W, RING, THREADS>), {0, 0}};
 }
 
 template <int VARIANT>
 void add_entries(std::vector<CullKernel> &v) {
-    v.push_back(cull_entry<VARIANT, 2, 256, 256>());
-    v.push_back(cull_entry<VARIANT, 2, 128, 256>());
-    v.push_back(cull_entry<VARIANT, 2, 256, 128>());
-    v.push_back(cull_entry<VARIANT, 2, 128, 128>());
-    v.push_back(cull_entry<VARIANT, 4, 256, 256>());
-    v.push_back(cull_entry<VARIANT, 4, 512, 256>());
-    v.push_back(cull_entry<VARIANT, 4, 256, 128>());
-    v.push_back(cull_entry<VARIANT, 4, 512, 128>());
+    constexpr int T = (int)HRR_TOP_LEVELS;
+    v.push_back(cull_entry<VARIANT, 2, 256, 256, 0>());
+    v.push_back(cull_entry<VARIANT, 2, 128, 256, 0>());
+    v.push_back(cull_entry<VARIANT, 2, 256, 128, 0>());
+    v.push_back(cull_entry<VARIANT, 2, 128, 128, 0>());
+    v.push_back(cull_entry<VARIANT, 2, 256, 256, T>());
+    v.push_back(cull_entry<VARIANT, 2, 128, 256, T>());
+    v.push_back(cull_entry<VARIANT, 2, 256, 128, T>());
+    v.push_back(cull_entry<VARIANT, 2, 128, 128, T>());
+    v.push_back(cull_entry<VARIANT, 4, 256, 256, 0>());
+    v.push_back(cull_entry<VARIANT, 4, 512, 256, 0>());
+    v.push_back(cull_entry<VARIANT, 4, 256, 128, 0>());
+    v.push_back(cull_entry<VARIANT, 4, 512, 128, 0>());
 }
 
 std::vector<CullKernel> &cull_kernels() {
@@ -52,7 +60,7 @@ std::vector<CullKernel> &cull_kernels() {
 CullKernel *cull_kernel_for(const hrr_tuning &t) {
     for (CullKernel &k : cull_kernels())
         if (k.variant == t.rangemin_variant && k.width == (int)t.node_width && k.ring == (int)t.ring_entries &&
-            k.threads == (int)t.threads_per_block)
+            k.threads == (int)t.threads_per_block && k.top == (int)hrr_tuning_top(t))
             return &k;
     return nullptr;
 }

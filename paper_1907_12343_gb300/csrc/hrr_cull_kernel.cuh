@@ -37,6 +37,18 @@
 // per warp in shared memory and appended to the output with one atomic per frame and
 // coalesced 8-byte stores.
 //
+// The head (forms with top levels, single frames of binary records): each block stages the
+// top HRR_TOP_LEVELS levels of the hierarchy in shared memory, and each eye starts by
+// evaluating the 62 nodes below the root there, one per lane in two passes, instead of
+// walking those levels one per step with 1, 2, 4, 8 and 16 lanes busy. The cull test is
+// monotone: a child's box lies inside its parent's, its maximum intensity is at most the
+// parent's and its range minimum at least the parent's, and the test culls at least as
+// much for each, so a node below the root is visited iff its own test passes, whatever its
+// ancestors' results. The head counts the root and the visited nodes above the deepest top
+// level as visits, tests the top's leaves, and pushes the visited nodes of the deepest top
+// level (with their argmins) as the stack the walk starts from: the same visited set, visit
+// count and accepted set as a walk from the root.
+//
 // One launch may cover many frames (a batch): the eye cursor then runs over the eyes of all
 // frames, each warp finds its eye's frame by binary search over the frames' cursor offsets,
 // and the frames' descriptors are read through the constant cache. Frames of different
@@ -297,8 +309,52 @@ __device__ __forceinline__ void visit(const float4 *wide, uint32_t n_lights, uin
     }
 }
 
-// The traversal over the frames F (F[0] alone for a single frame).
-template <int VARIANT, bool BATCH, int W, int RING, int THREADS>
+// The head of eye j's traversal over the top slots `top` (shared memory): stages the top's
+// accepted leaves, pushes the visited nodes of the deepest top level onto the empty ring,
+// and returns the visits it accounts for (the root and the visited nodes above that level).
+template <int VARIANT, bool BATCH, int W>
+__device__ __forceinline__ uint32_t head(const float4 *top, const Eye &E, const Frame *F, uint2 *wbuf, uint16_t *wfr,
+                                         uint32_t &cnt, int lane, uint32_t f, uint32_t j, uint2 *ring,
+                                         uint32_t &pushed) {
+    constexpr uint32_t kDeep = HRR_TOP_SLOTS / 2;  // first slot of the deepest top level
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t visits = 1, n = 0;  // the root
+#pragma unroll
+    for (uint32_t p = 0; p < (HRR_TOP_SLOTS + 31) / 32; ++p) {
+        const uint32_t s = 1u + (uint32_t)lane + 32u * p;  // slots 1 .. HRR_TOP_SLOTS - 1
+        bool vis = false;
+        uint32_t acc[W];
+#pragma unroll
+        for (int t = 0; t < W; ++t) acc[t] = kNone;
+        uint32_t node = 0, karg = 0;
+        if (s < HRR_TOP_SLOTS) {
+            const float4 a = top[3 * s], h = top[3 * s + 1], x = top[3 * s + 2];
+            const uint32_t kind = __float_as_uint(x.z);
+            const uint32_t first = __float_as_uint(h.w), last = __float_as_uint(x.x);
+            if (kind == HRR_TOP_INTERNAL) {
+                karg = range_argmin<VARIANT>(first, last + 1u, E.r, E.c);
+                vis = survives(E, a, h, karg);
+                node = __float_as_uint(x.y);
+            } else if (kind == HRR_TOP_LEAF &&
+                       hrr_leaf_accepts(__brev(first) + E.r, E.tau, a.x, a.y, a.z, a.w, E.x, E.y, E.z)) {
+                acc[0] = first;
+            }
+        }
+        const bool deep = s >= kDeep;
+        visits += __popc(__ballot_sync(0xFFFFFFFFu, vis && !deep));
+        const unsigned bp = __ballot_sync(0xFFFFFFFFu, vis && deep);
+        if (vis && deep) ring[n + __popc(bp & lt)] = make_uint2(node, karg);
+        n += __popc(bp);
+        if (__any_sync(0xFFFFFFFFu, acc[0] != kNone)) emit<BATCH, W>(F, wbuf, wfr, cnt, lane, f, j, acc);
+    }
+    __syncwarp();
+    pushed = n;
+    return visits;
+}
+
+// The traversal over the frames F (F[0] alone for a single frame); TOP levels of the
+// hierarchy evaluated by the head (0: none, the walk starts at the root).
+template <int VARIANT, bool BATCH, int W, int RING, int THREADS, int TOP>
 __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
     constexpr int kWarps = THREADS / 32;
     constexpr uint32_t kRing = RING;
@@ -307,9 +363,19 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
     // are resident (see the spill below), which needs kRing >= 32 W + 31
     static_assert((kRing & kRingMask) == 0 && kRing >= 32 * W + 32, "ring size");
     static_assert(kBuf >= 32 * W, "output staging buffer");
+    // the head reads one frame's binary records and pushes at most 32 entries
+    static_assert(TOP == 0 || (TOP == (int)HRR_TOP_LEVELS && W == 2 && !BATCH && kRing >= 32), "top levels");
     __shared__ uint2 buf[kWarps][kBuf];
     __shared__ uint16_t buf_frame[BATCH ? kWarps : 1][BATCH ? kBuf : 1];
     __shared__ uint2 ring_all[kWarps][kRing];  // (node, argmin of its range minimum)
+    __shared__ float4 top_s[TOP ? 3 * HRR_TOP_SLOTS : 1];
+    if constexpr (TOP > 0) {  // the top slots follow the frame's binary records
+        if (F[0].n_lights > 1) {
+            const float4 *src = F[0].nodes + 4 * (size_t)(F[0].n_lights - 1u);
+            for (uint32_t k = threadIdx.x; k < 3 * HRR_TOP_SLOTS; k += THREADS) top_s[k] = __ldg(&src[k]);
+        }
+        __syncthreads();
+    }
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -368,8 +434,13 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
         // Stack: logical entries [0, S); the newest R of them are in the ring at index & mask,
         // the others in the spill area at their logical index.
         uint32_t S = 1, R = 1, visits = 0;
-        if (lane == 0) ring[0] = make_uint2(0u, range_argmin<VARIANT>(0u, n_lights, E.r, E.c));
-        __syncwarp();
+        if constexpr (TOP > 0) {
+            visits = head<VARIANT, BATCH, W>(top_s, E, F, wbuf, wfr, cnt, lane, f, j, ring, S);
+            R = S;
+        } else {
+            if (lane == 0) ring[0] = make_uint2(0u, range_argmin<VARIANT>(0u, n_lights, E.r, E.c));
+            __syncwarp();
+        }
         while (S > 0) {
             if (visits >= n_lights) {  // each internal node is visited at most once per eye
                 if (lane == 0) atomicOr(Lc.flags, HRR_FLAG_TOPOLOGY);
@@ -457,16 +528,16 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
 
 // A single frame travels as a plain kernel parameter; a batch's frames as a grid-constant
 // array (indexed by the frame a warp is on).
-template <int VARIANT, int W, int RING, int THREADS>
+template <int VARIANT, int W, int RING, int THREADS, int TOP>
 __global__ void __launch_bounds__(THREADS, min_blocks<W>(THREADS))
 cull_single_kernel(const Launch Lc, const Frame fr) {
-    traverse<VARIANT, false, W, RING, THREADS>(Lc, &fr);
+    traverse<VARIANT, false, W, RING, THREADS, TOP>(Lc, &fr);
 }
 
 template <int VARIANT, int W, int RING, int THREADS>
 __global__ void __launch_bounds__(THREADS, min_blocks<W>(THREADS))
 cull_batch_kernel(const __grid_constant__ Launch Lc, const __grid_constant__ FrameArray<kMaxFrames> FA) {
-    traverse<VARIANT, true, W, RING, THREADS>(Lc, FA.f);
+    traverse<VARIANT, true, W, RING, THREADS, 0>(Lc, FA.f);
 }
 
 }  // namespace

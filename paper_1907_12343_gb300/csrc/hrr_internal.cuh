@@ -78,22 +78,42 @@ struct hrr_ctx {
     std::string err;
 };
 
+// The top of a hierarchy, which the traversal's head evaluates from shared memory: the
+// nodes of depth 0 .. HRR_TOP_LEVELS - 1 in heap order (slot 0 the root, the children of
+// slot s in slots 2s + 1 and 2s + 2), three float4 per slot:
+//   (box low corner, maximum intensity), (box high corner, first leaf as bits),
+//   (last leaf as bits, node index as bits, kind as bits, 0)
+// with kind HRR_TOP_EMPTY (no node: below a leaf), HRR_TOP_INTERNAL or HRR_TOP_LEAF (a light:
+// its position and intensity, first = last = its sorted position). The root's box is not
+// stored (the root is never tested). The slots follow the tree's binary records in the same
+// allocation, at float4 offset 4 (n - 1).
+#define HRR_TOP_LEVELS 6u
+#define HRR_TOP_SLOTS 63u  // 2^HRR_TOP_LEVELS - 1
+#define HRR_TOP_BYTES (HRR_TOP_SLOTS * 3u * 16u)
+enum : uint32_t { HRR_TOP_EMPTY = 0u, HRR_TOP_INTERNAL = 1u, HRR_TOP_LEAF = 2u };
+
 struct hrr_tree {
     int device = 0;
     uint32_t n = 0;
     uint32_t height = 0;
-    hrr_node *nodes = nullptr;  // n - 1 records (one record with the single leaf if n == 1)
+    // n - 1 records (one record with the single leaf if n == 1), followed by the top slots
+    hrr_node *nodes = nullptr;
     uint32_t *perm = nullptr;   // n
     // The same hierarchy read with nodes of width four: for every internal node g a
-    // 128-byte record of its four grandchild slots (hrr_widen_enqueue), at index g; a
+    // 128-byte record of its four grandchild slots (hrr_derived_enqueue), at index g; a
     // traversal of width four reads the even-depth ones only. One record (the leaf in
     // slot 0) when n == 1.
     float4 *wide = nullptr;
 };
 
-// Fill tree->wide from tree->nodes (one thread per internal node); skipped when *flags
-// holds HRR_FLAG_NONFINITE (a failed refit leaves the hierarchy as it was).
-cudaError_t hrr_widen_enqueue(hrr_tree *tree, const unsigned long long *flags, cudaStream_t st);
+// Fill the records derived from the binary ones: the top slots after tree->nodes, and
+// tree->wide if the tree has it (one thread per internal node); skipped when *flags holds
+// HRR_FLAG_NONFINITE (a failed refit leaves the hierarchy as it was).
+cudaError_t hrr_derived_enqueue(hrr_tree *tree, const unsigned long long *flags, cudaStream_t st);
+// Kernels hrr_derived_enqueue launches for the tree.
+inline int hrr_derived_launches(const hrr_tree *tree) { return tree->wide ? 2 : 1; }
+// Kernels a refit launches (hrr_refit_enqueue).
+inline int hrr_refit_launches(const hrr_tree *tree) { return (tree->n > 1 ? 3 : 1) + hrr_derived_launches(tree); }
 
 // Layer (sample mod d) of a w x h x d tile: the shifts one culling pass uses.
 inline const uint32_t *hrr_tile_layer(const uint32_t *tile, uint32_t w, uint32_t h, uint32_t d,
@@ -143,18 +163,25 @@ struct hrr_cull_frame_t {
     unsigned long long cursor_begin; // where the frame's eyes start on the launch's cursor
 };
 
-// Traversal defaults: node width, shared-memory stack ring per warp, threads per block.
+// Traversal defaults: node width, shared-memory stack ring per warp, threads per block,
+// top levels evaluated from shared memory (1: the root only, every level walked).
 #define HRR_DEFAULT_NODE_WIDTH 2u
 #define HRR_DEFAULT_RING 256u
 #define HRR_DEFAULT_THREADS 128u
+#define HRR_DEFAULT_TOP_LEVELS HRR_TOP_LEVELS
 
 // Launch parameters with the library defaults filled in.
 inline hrr_tuning hrr_tuning_normalized(hrr_tuning t) {
     if (!t.node_width) t.node_width = HRR_DEFAULT_NODE_WIDTH;
     if (!t.ring_entries) t.ring_entries = HRR_DEFAULT_RING;
     if (!t.threads_per_block) t.threads_per_block = HRR_DEFAULT_THREADS;
+    // the top levels come with binary records only: width four defaults to the root alone
+    if (!t.top_levels) t.top_levels = t.node_width == 2 ? HRR_DEFAULT_TOP_LEVELS : 1u;
     return t;
 }
+// Levels the traversal's head evaluates from shared memory for a normalised tuning (0 = no
+// head: the traversal starts at the root).
+inline uint32_t hrr_tuning_top(const hrr_tuning &t) { return t.top_levels == 1u ? 0u : t.top_levels; }
 inline hrr_tuning hrr_tuning_of(const hrr_cull_opts &o) {
     hrr_tuning t{};
     t.rangemin_variant = o.rangemin_variant;
@@ -162,6 +189,7 @@ inline hrr_tuning hrr_tuning_of(const hrr_cull_opts &o) {
     t.node_width = o.node_width;
     t.ring_entries = o.ring_entries;
     t.threads_per_block = o.threads_per_block;
+    t.top_levels = o.top_levels;
     return hrr_tuning_normalized(t);
 }
 // Every combination that has a compiled traversal (zero fields stand for the defaults).
@@ -169,6 +197,7 @@ inline bool hrr_tuning_valid(const hrr_tuning &t0) {
     const hrr_tuning t = hrr_tuning_normalized(t0);
     if ((t.rangemin_variant != 0 && t.rangemin_variant != 2) || t.blocks_per_sm > 64) return false;
     if (t.threads_per_block != 128 && t.threads_per_block != 256) return false;
+    if (t.top_levels != 1u && (t.top_levels != HRR_TOP_LEVELS || t.node_width != 2)) return false;
     if (t.node_width == 2) return t.ring_entries == 128 || t.ring_entries == 256;
     if (t.node_width == 4) return t.ring_entries == 256 || t.ring_entries == 512;
     return false;

@@ -232,7 +232,7 @@ bool enqueue_slice(hrr_server *s, int k) {
             } else {
                 if (hrr_refit_enqueue(const_cast<hrr_tree *>(j->desc.tree), j->desc.refit, scratch,
                                       s->dev_counts + kSlotWords * (size_t)j->slot + 2, st) == cudaSuccess)
-                    s->launches += j->desc.tree->n > 1 ? 4 : 2;
+                    s->launches += hrr_refit_launches(j->desc.tree);
                 cudaFreeAsync(scratch, st);
             }
         }

@@ -1,8 +1,8 @@
 // Autotuning of the traversal's form and launch shape.
 //
 // The traversal's results do not depend on its tuning (range-minimum variant, node width,
-// shared-memory stack ring, threads per block, resident blocks per SM); only its speed
-// does. hrr_autotune_all times every compiled form, at the most resident blocks per SM that
+// shared-memory stack ring, threads per block, top levels evaluated from shared memory,
+// resident blocks per SM); only its speed does. hrr_autotune_all times every compiled form, at the most resident blocks per SM that
 // fit and at one block fewer, on a caller-given eye sample; hrr_autotune keeps the fastest.
 // A caller (the Python autotuner) caches one answer per size class of workload.
 #include <algorithm>
@@ -17,20 +17,22 @@ std::vector<hrr_tuning> candidates() {
     std::vector<hrr_tuning> out;
     for (int variant : {0, 2})
         for (uint32_t width : {2u, 4u})
-            for (uint32_t ring : {128u, 256u, 512u})
-                for (uint32_t threads : {128u, 256u}) {
-                    hrr_tuning t{};
-                    t.rangemin_variant = variant;
-                    t.node_width = width;
-                    t.ring_entries = ring;
-                    t.threads_per_block = threads;
-                    if (!hrr_tuning_valid(t)) continue;
-                    const int most = hrr_cull_max_blocks(t, false);
-                    for (int b = most; b >= std::max(1, most - 1); --b) {
-                        t.blocks_per_sm = (uint32_t)b;
-                        out.push_back(t);
+            for (uint32_t top : {1u, HRR_TOP_LEVELS})
+                for (uint32_t ring : {128u, 256u, 512u})
+                    for (uint32_t threads : {128u, 256u}) {
+                        hrr_tuning t{};
+                        t.rangemin_variant = variant;
+                        t.node_width = width;
+                        t.ring_entries = ring;
+                        t.threads_per_block = threads;
+                        t.top_levels = top;
+                        if (!hrr_tuning_valid(t)) continue;
+                        const int most = hrr_cull_max_blocks(t, false);
+                        for (int b = most; b >= std::max(1, most - 1); --b) {
+                            t.blocks_per_sm = (uint32_t)b;
+                            out.push_back(t);
+                        }
                     }
-                }
     return out;
 }
 
@@ -61,6 +63,7 @@ extern "C" int hrr_autotune_all(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, co
         o.node_width = t.node_width;
         o.ring_entries = t.ring_entries;
         o.threads_per_block = t.threads_per_block;
+        o.top_levels = t.top_levels;
         std::vector<double> ts;
         for (int rep = 0; rep < 4 && status == HRR_OK; ++rep) {
             uint64_t count = 0;
@@ -88,8 +91,8 @@ extern "C" int hrr_autotune(hrr_ctx *ctx, hrr_eyes eyes, uint32_t n_eyes, const 
                             double *best_ms) {
     if (!ctx) return HRR_ERR_INVALID_ARG;
     if (!best) return hrr_fail(ctx, HRR_ERR_INVALID_ARG, "best is NULL");
-    std::vector<hrr_tuning> tried(64);
-    std::vector<double> ms(64);
+    std::vector<hrr_tuning> tried(128);
+    std::vector<double> ms(128);
     uint32_t n = 0;
     const int st = hrr_autotune_all(ctx, eyes, n_eyes, tree, tau, dev_pairs, cap, tried.data(), ms.data(),
                                     (uint32_t)tried.size(), &n);

@@ -31,12 +31,19 @@ def _gpu(ctx, s, **kw):
     return res
 
 
-FORMS = [{"node_width": w, "ring_entries": r, "threads_per_block": th}
-         for w, rings in ((2, (128, 256)), (4, (256, 512))) for r in rings for th in (128, 256)]
+# every compiled form: node width, stack ring, threads per block, and for binary records the
+# top levels evaluated from shared memory (1: walked from the root)
+FORMS = [{"node_width": w, "ring_entries": r, "threads_per_block": th, "top_levels": top}
+         for w, rings, tops in ((2, (128, 256), (1, 6)), (4, (256, 512), (1,)))
+         for r in rings for th in (128, 256) for top in tops]
+FORM_ID = "w{node_width}r{ring_entries}t{threads_per_block}top{top_levels}".format
+# the node width and top levels alone (the other fields at their defaults)
+SHAPES = [{"node_width": 2, "top_levels": 1}, {"node_width": 2, "top_levels": 6}, {"node_width": 4}]
+SHAPE_ID = lambda f: "w{}top{}".format(f["node_width"], f.get("top_levels", 1))
 
 
 @pytest.mark.parametrize("variant", [0, 2])
-@pytest.mark.parametrize("form", FORMS, ids=lambda f: "w{node_width}r{ring_entries}t{threads_per_block}".format(**f))
+@pytest.mark.parametrize("form", FORMS, ids=lambda f: FORM_ID(**f))
 def test_uniform_tiny_scene_equals_flat(ctx, variant, form):
     # 1024 eyes x 4096 lights, 32x32 tile, tau for ~32 accepted per eye, in every compiled
     # form of the traversal (node width, stack ring, threads per block)
@@ -52,12 +59,13 @@ def test_uniform_tiny_scene_equals_flat(ctx, variant, form):
     assert v_total == hier["total_visits"] and acc == cnt == len(flat["pairs"])
 
 
-@pytest.mark.parametrize("width", [2, 4])
-def test_ragged_frame_equals_oracle(ctx, width):
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_ID)
+def test_ragged_frame_equals_oracle(ctx, shape):
     # eye count not a multiple of the warp or block size, light count not a power of two
     s = synth.scene_frame(width=257, height=131, n_lights=50021, tile_w=64, tile_h=64,
                           target=64.0, seed=7)
-    st, cnt, pairs, vis = _gpu(ctx, s, visits=True, tuning={"node_width": width})
+    width = shape["node_width"]
+    st, cnt, pairs, vis = _gpu(ctx, s, visits=True, tuning=shape)
     assert st == 0
     t = oracle.Tree(s.light_pos, s.intensity)
     hier = oracle_hier(t, s.eye_pos, s.px, s.py, s.tile, s.tau, width=width)
@@ -119,19 +127,49 @@ def test_largest_batch_frame_sampled(ctx):
     assert np.array_equal(vis.cpu().numpy().view(np.uint32)[ids], hier["visits"].astype(np.uint32))
 
 
-@pytest.mark.parametrize("width", [2, 4])
-@pytest.mark.parametrize("n_lights", [1, 2, 3, 4, 5, 33])
-def test_tiny_light_sets(ctx, n_lights, width):
-    s = dict(synth.scene_uniform(n_lights=64, grid_w=16, grid_h=8, tile_w=8, tile_h=8,
+@pytest.mark.parametrize("shape", SHAPES, ids=SHAPE_ID)
+@pytest.mark.parametrize("n_lights", [1, 2, 3, 4, 5, 33, 63, 64, 65])
+def test_tiny_light_sets(ctx, n_lights, shape):
+    # trees whose top levels hold leaves and empty slots (up to 63 lights: all of the tree)
+    s = dict(synth.scene_uniform(n_lights=65, grid_w=16, grid_h=8, tile_w=8, tile_h=8,
                                  target=4.0, seed=9))
     s["light_pos"] = s["light_pos"][:n_lights]
     s["intensity"] = s["intensity"][:n_lights]
     s["tau"] = np.float32(s["tau"] * 20)
-    st, cnt, pairs, vis = _gpu(ctx, s, visits=True, tuning={"node_width": width})
+    width = shape["node_width"]
+    st, cnt, pairs, vis = _gpu(ctx, s, visits=True, tuning=shape)
     assert st == 0
     t = oracle.Tree(s["light_pos"], s["intensity"])
     flat = oracle.cull_flat(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"])
     hier = oracle_hier(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"], width=width)
+    assert np.array_equal(sorted_pairs(pairs), sorted_pairs(flat["pairs"]))
+    assert np.array_equal(vis, hier["visits"].astype(np.uint32))
+
+
+@pytest.mark.parametrize("topology", ["radix", "cost"])
+@pytest.mark.parametrize("top", [1, 6])
+def test_leaves_near_the_root(ctx, top, topology):
+    # lights at x = 2^-1 .. 2^-21 beside a dense cluster at the origin: the radix tree cuts
+    # them off one by one (leaves at depths 1, 3, 4 and 5), the cost-driven tree at depths
+    # 4 and 5, so the top levels mix leaves, internal nodes and empty slots; pairs equal the
+    # flat oracle and visits the hierarchical one
+    rng = np.random.default_rng(5)
+    x = (2.0 ** -np.arange(1, 22, dtype=np.float64)).astype(np.float32)
+    line = np.stack([x, np.full_like(x, 0.5), np.full_like(x, 0.5)], axis=1)
+    pos = np.concatenate([line, (rng.random((3000, 3)) * 1e-3).astype(np.float32)]).astype(np.float32)
+    inten = np.ones(len(pos), np.float32)
+    s = dict(synth.scene_uniform(n_lights=16, grid_w=32, grid_h=16, tile_w=16, tile_h=16, seed=13))
+    s["light_pos"], s["intensity"], s["tau"] = pos, inten, np.float32(1e-3)
+    g = upload_scene(s)
+    ctx.set_shift_tile(s["tile"])
+    tree = ctx.build_light_tree(g["lx"], g["ly"], g["lz"], g["li"], topology=topology)
+    st, cnt, pairs, vis = run_cull(ctx, g, tree, float(s["tau"]), visits=True,
+                                   tuning={"node_width": 2, "top_levels": top})
+    tree.free()
+    assert st == 0 and cnt > 0
+    t = oracle.Tree(pos, inten, topology=topology)
+    flat = oracle.cull_flat(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"])
+    hier = oracle_hier(t, s["eye_pos"], s["px"], s["py"], s["tile"], s["tau"], width=2)
     assert np.array_equal(sorted_pairs(pairs), sorted_pairs(flat["pairs"]))
     assert np.array_equal(vis, hier["visits"].astype(np.uint32))
 
