@@ -281,11 +281,11 @@ def run_ours(args):
 
 # Algorithmic work of one node visit on the frame workload with the cost-driven hierarchy
 # (counted with the oracle's traversal over 3,000 evenly spaced eyes): 1.960 internal child
-# tests x 21 ops (the box gap, 9; its square, 3 with fused multiply-adds; the distance floor
-# and the scaled bound, 4; the value of the range minimum, 2; the division-free cull
+# tests x 19 ops (the box gap, 9; its square, 3 with fused multiply-adds; the distance floor
+# and the scaled bound, 2; the value of the range minimum, 2; the division-free cull
 # comparison, 3) + 0.973 new range minima x 51 integer ops + 0.988 inherited minima x 2 +
 # 0.040 leaf tests x 17.
-OPS_PER_VISIT = 1.960 * 21 + 0.973 * 51 + 0.988 * 2 + 0.040 * 17
+OPS_PER_VISIT = 1.960 * 19 + 0.973 * 51 + 0.988 * 2 + 0.040 * 17
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_1920x1080.md")
 PROFILE_SMALL = os.path.join(ROOT, "profiles", "cull_single_kernel_frame_480x270.md")
 TOPOLOGY = "cost"  # hierarchy shape of the benchmarked builds (set from --topology)

@@ -416,14 +416,16 @@ static float u32_to_float_rd(uint32_t v)
  * every light inside. Per axis the gap to the box is max(0, RD(lo - e), RD(e - hi)); the
  * squared gaps are summed with fused multiply-adds rounded down and floored at 1e-4:
  * den_D <= the float32 max(d^2, 1e-4) of any light in the box. With the scale
- * tau' = tau 2^32 (exact), num_U = RU(tau' max(imax, 0)) >= 2^32 RN(tau I) of any of them
- * (when tau imax is a normal float), and each light's quotient RN(RN(tau I) / den) is at
- * most its numerator over den_D times (1 + 2^-24). So the node is culled iff
- *     RD(RD(v) den_D) >= RU(num_U (1 + 2^-23)),
- * a division-free test whose left side is a lower bound of v den_D and right side an upper
- * bound of 2^32 num (1 + 2^-24). Outside that chain it is sound too: v = 0 culls only when
- * the right side is 0 (no light below has p > 0); if tau imax is subnormal every
- * threshold is at most 1 and a cull needs v >= 1; an infinite right side never culls. */
+ * s = RU(tau' (1 + 2^-22)), tau' = tau 2^32 (exact), the right side RU(s imax) is at least
+ * tau' imax (1 + 2^-22) >= 2^32 RN(tau I) (1 + 2^-24)(1 + 2^-23) for any light with
+ * 0 < I <= imax (when tau I is a normal float), and each light's quotient
+ * RN(RN(tau I) / den) is at most its numerator over den_D times (1 + 2^-24). So the node is
+ * culled iff
+ *     RD(RD(v) den_D) >= RU(s imax),
+ * a division-free test whose left side is a lower bound of v den_D. Outside that chain it
+ * is sound too: a right side <= 0 (tau imax <= 0: no light below has p > 0) culls at any v,
+ * and otherwise v = 0 never culls; if tau I is subnormal the light's threshold is at most
+ * 1 and a cull needs v >= 1; a right side of +inf or NaN (tau' overflows) never culls. */
 int or_node_culls(float tau, const float lo[3], const float hi[3], float imax, const float e[3],
                   uint32_t v)
 {
@@ -438,8 +440,8 @@ int or_node_culls(float tau, const float lo[3], const float hi[3], float imax, c
     d2 = fma_rd(g[2], g[2], d2);
     float den = fmaxf(d2, kMinDist2);
     float tau32 = tau * 4294967296.0f; /* exact: a power-of-two scaling */
-    float num = mul_ru(tau32, fmaxf(imax, 0.0f));
-    float rhs = mul_ru(num, 1.00000012f); /* 1 + 2^-23 */
+    float scale = mul_ru(tau32, 1.0f + 0x1p-22f);
+    float rhs = mul_ru(scale, imax);
     float lhs = mul_rd(u32_to_float_rd(v), den);
     return lhs >= rhs;
 }

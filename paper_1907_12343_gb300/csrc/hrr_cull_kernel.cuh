@@ -190,7 +190,7 @@ __device__ __forceinline__ uint32_t range_argmin(uint32_t a, uint32_t b, uint32_
 // The eye a traversal works on.
 struct Eye {
     float x, y, z, tau;
-    float tau32;    // tau 2^32, the node test's scale
+    float scale;    // the node test's scale, hrr_node_scale(tau)
     uint32_t r, c;  // shift and brev(2^32 - r)
 };
 
@@ -206,7 +206,7 @@ struct Visit {
 // its range minimum at argmin k culls it; the box is (lo, imax, hi).
 __device__ __forceinline__ bool survives(const Eye &E, const float4 &lo, const float4 &hi, uint32_t k) {
     float den, rhs;
-    hrr_node_bound(E.tau32, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w, E.x, E.y, E.z, den, rhs);
+    hrr_node_bound(E.scale, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w, E.x, E.y, E.z, den, rhs);
     return !hrr_node_culls(__brev(k) + E.r, den, rhs);
 }
 
@@ -227,9 +227,9 @@ __device__ __forceinline__ void visit(const float4 *nodes, uint32_t n_lights, ui
     }
     const bool int0 = first != split, int1 = split + 1u != last;
     const bool kin0 = kmin <= split;
-    uint32_t knew = kNone;
-    if (kin0 ? int1 : int0)
-        knew = range_argmin<VARIANT>(kin0 ? split + 1u : first, kin0 ? last + 1u : split + 1u, E.r, E.c);
+    // the other child's argmin (unused when that child is a leaf: computing it anyway
+    // keeps the warp on one path)
+    const uint32_t knew = range_argmin<VARIANT>(kin0 ? split + 1u : first, kin0 ? last + 1u : split + 1u, E.r, E.c);
     V.karg[0] = kin0 ? kmin : knew;
     V.karg[1] = kin0 ? knew : kmin;
     V.node[0] = split;
@@ -415,7 +415,7 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
         E.y = fr.ey[j];
         E.z = fr.ez[j];
         E.tau = fr.tau;
-        E.tau32 = fr.tau * 4294967296.0f;  // exact
+        E.scale = hrr_node_scale(fr.tau);
         const uint32_t tx = fr.px[j] % fr.tile_w, ty = fr.py[j] % fr.tile_h;
         E.r = fr.tile[ty * fr.tile_w + tx] + fr.shift_offset;
         if (n_lights == 1) {  // the root is a leaf (record 0, slot 0, in either layout)

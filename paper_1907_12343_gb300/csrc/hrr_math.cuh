@@ -145,20 +145,26 @@ __device__ __forceinline__ float hrr_max3(float a, float b, float c) {
     return d;
 }
 
+// The node test's scale for a frame's tau: RU(tau 2^32 (1 + 2^-22)); tau 2^32 is exact (a
+// power-of-two scaling), infinite when it overflows.
+__device__ __forceinline__ float hrr_node_scale(float tau) {
+    return __fmul_ru(tau * 4294967296.0f, 1.0f + 0x1p-22f);
+}
+
 // Conservative cull test of a node with box [lo, hi] and maximum intensity imax, for an eye
-// at e, with the culling scale given as tau32 = tau 2^32 (exact: a power-of-two scaling).
+// at e, with the scale s = hrr_node_scale(tau):
 //   den = max(d2, 1e-4), d2 = RD(gz^2 + RD(gy^2 + RD(gx^2))) (fused, rounded down) with
 //         per-axis gaps g = max(0, RD(lo - e), RD(e - hi)): at most the float32 max(d^2, 1e-4)
 //         of any light in the box;
-//   rhs = RU(RU(tau32 max(imax, 0)) (1 + 2^-23)): at least 2^32 RN(tau I) (1 + 2^-23) of
-//         every light, when tau max(imax, 0) is a normal float.
-// The node is culled at range minimum v iff RD(RD(v) den) >= rhs. Then for every light i,
+//   rhs = RU(s imax) >= 2^32 tau imax (1 + 2^-22) >= 2^32 RN(tau I) (1 + 2^-24)(1 + 2^-23) of
+//         every light with 0 < I <= imax, when tau I is a normal float.
+// The node is culled at range minimum v iff RD(RD(v) den) >= rhs. Then for every such light,
 // v den_i >= 2^32 RN(tau I_i) (1 + 2^-23) >= 2^32 RN(RN(tau I_i) / den_i), so v is at least
-// its threshold ceil(p_i 2^32). The cases outside that chain are sound as well: v = 0 culls
-// only when rhs = 0 (tau max(imax, 0) = 0: no light below has p > 0); if tau I is
-// subnormal every light's threshold is at most 1 and a cull needs v >= 1 (rhs > 0); an
-// infinite rhs never culls.
-__device__ __forceinline__ void hrr_node_bound(float tau32, float lox, float loy, float loz,
+// its threshold ceil(p_i 2^32). The cases outside that chain are sound as well: rhs <= 0
+// (tau imax <= 0: no light below has p > 0) culls at any v, v = 0 included, and otherwise
+// v = 0 never culls; if tau I is subnormal the light's threshold is at most 1 and a cull
+// needs v >= 1 (rhs > 0); rhs = +inf or NaN (tau 2^32 overflows) never culls.
+__device__ __forceinline__ void hrr_node_bound(float scale, float lox, float loy, float loz,
                                                float hix, float hiy, float hiz, float imax,
                                                float ex, float ey, float ez, float &den,
                                                float &rhs) {
@@ -169,7 +175,7 @@ __device__ __forceinline__ void hrr_node_bound(float tau32, float lox, float loy
     d2 = __fmaf_rd(gy, gy, d2);
     d2 = __fmaf_rd(gz, gz, d2);
     den = fmaxf(d2, 1e-4f);
-    rhs = __fmul_ru(__fmul_ru(tau32, fmaxf(imax, 0.0f)), 1.00000012f);
+    rhs = __fmul_ru(scale, imax);
 }
 
 __device__ __forceinline__ bool hrr_node_culls(uint32_t v, float den, float rhs) {

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cull_samples_kernel(cons
     uint2 *const spill = P.spill + ((size_t)blockIdx.x * kWarps + warp) * P.spill_cap;
     const uint32_t all = P.n_samples >= 32 ? 0xFFFFFFFFu : (1u << P.n_samples) - 1u;
     const float tau = P.tau;
-    const float tau32 = P.tau * 4294967296.0f;  // the node test's scale (exact)
+    const float scale = hrr_node_scale(P.tau);  // the node test's scale
     uint32_t cnt = 0;
     unsigned long long node_visits = 0, sample_visits = 0;
 
@@ -195,8 +195,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cull_samples_kernel(cons
                     valid = true;
                     int0 = first != split;
                     int1 = split + 1u != last;
-                    hrr_node_bound(tau32, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q0.w, ex, ey, ez, den0, rhs0);
-                    hrr_node_bound(tau32, q2.x, q2.y, q2.z, q3.x, q3.y, q3.z, q2.w, ex, ey, ez, den1, rhs1);
+                    hrr_node_bound(scale, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q0.w, ex, ey, ez, den0, rhs0);
+                    hrr_node_bound(scale, q2.x, q2.y, q2.z, q3.x, q3.y, q3.z, q2.w, ex, ey, ez, den1, rhs1);
                 }
             }
             // per sample: the children's range minima and cull tests, or the leaf tests
