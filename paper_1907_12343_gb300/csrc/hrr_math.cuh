@@ -95,6 +95,8 @@ __device__ __forceinline__ uint32_t hrr_rangemin_closed(uint32_t a, uint32_t b, 
 //     X = i0 - q, Y = (b - 1 - q) rounded down to a multiple of P) the smallest Phi_2 is
 //     at the one with the most trailing zeros, Y with the bits below
 //     fls((X - P) xor Y) cleared (or q itself when X = 0).
+//   * P - 1 is all ones shifted right by clz(mask) (a clamped shift: 0 in case three), and
+//     2^ks its top bit; the bits below fls(t) are all ones shifted right by clz(t) + 1.
 __device__ __forceinline__ uint32_t hrr_range_argmin_select(uint32_t a, uint32_t b, uint32_t c) {
     const uint32_t L = b - a;
     const uint32_t D = c - a;
@@ -106,15 +108,15 @@ __device__ __forceinline__ uint32_t hrr_range_argmin_select(uint32_t a, uint32_t
     if (((D & bh) != 0u) || (D & mh) < (L & mh)) levels |= Z & bh;
     const uint32_t hiD = (D >> h) >> 1;
     if ((D & (mh | bh)) < L && hiD != 0u) levels |= Z & (bh << __ffs(hiD));  // bit K
-    const int ks = 31 - __clz(levels);  // -1 when no level: case three
-    const uint32_t bit = ks >= 0 ? (1u << (ks & 31)) : 0u;
-    const uint32_t pm = ks >= 0 ? ((bit << 1) - 1u) : 0u;  // P - 1 (all ones when ks = 31)
+    const uint32_t pm = __funnelshift_rc(0xFFFFFFFFu, 0u, (uint32_t)__clz(levels));  // P - 1
+    const uint32_t bit = pm & ~(pm >> 1);                                            // 2^ks
     const uint32_t i0 = a + ((D ^ bit) & pm);
     const uint32_t q = i0 & pm;
     const uint32_t X = i0 & ~pm;
     const uint32_t Y = (b - 1u - q) & ~pm;
-    const uint32_t g = 31u - __clz((X - pm - 1u) ^ Y);  // X - P; X >= P whenever X != 0
-    const uint32_t k = X == 0u ? q : (q | (Y & (0u - (1u << g))));
+    // (X - P) xor Y is nonzero whenever X != 0 (X - P < X <= Y); the 1 keeps clz below 32
+    const uint32_t t = ((X - pm - 1u) ^ Y) | 1u;
+    const uint32_t k = X == 0u ? q : (q | (Y & ~(0x7FFFFFFFu >> __clz(t))));
     return D < L ? c : k;
 }
 
