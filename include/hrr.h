@@ -128,7 +128,8 @@ typedef struct hrr_cull_opts {
      *     The cull test is monotone (a child's smaller box, smaller maximum intensity and
      *     larger range minimum never turn its parent's cull into a visit), so a node below
      *     the root is visited iff its own test passes, and those levels need not be walked
-     *     one level per step. Batched launches of several frames walk from the root. */
+     *     one level per step. Batched launches of several frames read each frame's top
+     *     slots from global memory instead. */
     uint32_t node_width;
     uint32_t ring_entries;
     uint32_t threads_per_block;

@@ -14,8 +14,7 @@ namespace {
 
 // One compiled form of the traversal: range-minimum variant, node width, ring entries per
 // warp, threads per block and top levels evaluated by the head, with its single-frame and
-// batched kernels (batched launches of several frames walk from the root: a form with top
-// levels shares the batched kernel of its form without them).
+// batched kernels.
 struct CullKernel {
     int variant, width, ring, threads, top;
     const void *single, *batch;
@@ -26,7 +25,7 @@ template <int VARIANT, int W, int RING, int THREADS, int TOP>
 CullKernel cull_entry() {
     return {VARIANT, W, RING, THREADS, TOP,
             reinterpret_cast<const void *>(cull_single_kernel<VARIANT, W, RING, THREADS, TOP>),
-            reinterpret_cast<const void *>(cull_batch_kernel<VARIANT, W, RING, THREADS>), {0, 0}};
+            reinterpret_cast<const void *>(cull_batch_kernel<VARIANT, W, RING, THREADS, TOP>), {0, 0}};
 }
 
 template <int VARIANT>

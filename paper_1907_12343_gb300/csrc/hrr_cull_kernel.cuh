@@ -37,10 +37,12 @@
 // per warp in shared memory and appended to the output with one atomic per frame and
 // coalesced 8-byte stores.
 //
-// The head (forms with top levels, single frames of binary records): each block stages the
-// top HRR_TOP_LEVELS levels of the hierarchy in shared memory, and each eye starts by
-// evaluating the 62 nodes below the root there, one per lane in two passes, instead of
-// walking those levels one per step with 1, 2, 4, 8 and 16 lanes busy. The cull test is
+// The head (forms with top levels, binary records): each eye starts by evaluating the 62
+// nodes below the root of the top HRR_TOP_LEVELS levels, one per lane in two passes,
+// instead of walking those levels one per step with 1, 2, 4, 8 and 16 lanes busy. A
+// single-frame launch stages the top slots in shared memory once per block; in a batched
+// launch, whose warps move between frames, each eye reads its frame's slots (3 KB, cached
+// in L1 and L2) directly. The cull test is
 // monotone: a child's box lies inside its parent's, its maximum intensity is at most the
 // parent's and its range minimum at least the parent's, and the test culls at least as
 // much for each, so a node below the root is visited iff its own test passes, whatever its
@@ -309,9 +311,10 @@ __device__ __forceinline__ void visit(const float4 *wide, uint32_t n_lights, uin
     }
 }
 
-// The head of eye j's traversal over the top slots `top` (shared memory): stages the top's
-// accepted leaves, pushes the visited nodes of the deepest top level onto the empty ring,
-// and returns the visits it accounts for (the root and the visited nodes above that level).
+// The head of eye j's traversal over the top slots `top` (shared memory for a single frame,
+// global memory for a batch): stages the top's accepted leaves, pushes the visited nodes of
+// the deepest top level onto the empty ring, and returns the visits it accounts for (the
+// root and the visited nodes above that level).
 template <int VARIANT, bool BATCH, int W>
 __device__ __forceinline__ uint32_t head(const float4 *top, const Eye &E, const Frame *F, uint2 *wbuf, uint16_t *wfr,
                                          uint32_t &cnt, int lane, uint32_t f, uint32_t j, uint2 *ring,
@@ -328,7 +331,16 @@ __device__ __forceinline__ uint32_t head(const float4 *top, const Eye &E, const 
         for (int t = 0; t < W; ++t) acc[t] = kNone;
         uint32_t node = 0, karg = 0;
         if (s < HRR_TOP_SLOTS) {
-            const float4 a = top[3 * s], h = top[3 * s + 1], x = top[3 * s + 2];
+            float4 a, h, x;
+            if constexpr (BATCH) {
+                a = __ldg(&top[3 * s]);
+                h = __ldg(&top[3 * s + 1]);
+                x = __ldg(&top[3 * s + 2]);
+            } else {
+                a = top[3 * s];
+                h = top[3 * s + 1];
+                x = top[3 * s + 2];
+            }
             const uint32_t kind = __float_as_uint(x.z);
             const uint32_t first = __float_as_uint(h.w), last = __float_as_uint(x.x);
             if (kind == HRR_TOP_INTERNAL) {
@@ -363,13 +375,14 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
     // are resident (see the spill below), which needs kRing >= 32 W + 31
     static_assert((kRing & kRingMask) == 0 && kRing >= 32 * W + 32, "ring size");
     static_assert(kBuf >= 32 * W, "output staging buffer");
-    // the head reads one frame's binary records and pushes at most 32 entries
-    static_assert(TOP == 0 || (TOP == (int)HRR_TOP_LEVELS && W == 2 && !BATCH && kRing >= 32), "top levels");
+    // the head reads the frames' binary records and pushes at most 32 entries
+    static_assert(TOP == 0 || (TOP == (int)HRR_TOP_LEVELS && W == 2 && kRing >= 32), "top levels");
     __shared__ uint2 buf[kWarps][kBuf];
     __shared__ uint16_t buf_frame[BATCH ? kWarps : 1][BATCH ? kBuf : 1];
     __shared__ uint2 ring_all[kWarps][kRing];  // (node, argmin of its range minimum)
-    __shared__ float4 top_s[TOP ? 3 * HRR_TOP_SLOTS : 1];
-    if constexpr (TOP > 0) {  // the top slots follow the frame's binary records
+    constexpr bool kTopShared = TOP > 0 && !BATCH;
+    __shared__ float4 top_s[kTopShared ? 3 * HRR_TOP_SLOTS : 1];
+    if constexpr (kTopShared) {  // the top slots follow the frame's binary records
         if (F[0].n_lights > 1) {
             const float4 *src = F[0].nodes + 4 * (size_t)(F[0].n_lights - 1u);
             for (uint32_t k = threadIdx.x; k < 3 * HRR_TOP_SLOTS; k += THREADS) top_s[k] = __ldg(&src[k]);
@@ -435,7 +448,8 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
         // the others in the spill area at their logical index.
         uint32_t S = 1, R = 1, visits = 0;
         if constexpr (TOP > 0) {
-            visits = head<VARIANT, BATCH, W>(top_s, E, F, wbuf, wfr, cnt, lane, f, j, ring, S);
+            const float4 *top = kTopShared ? top_s : nodes + 4 * (size_t)(n_lights - 1u);
+            visits = head<VARIANT, BATCH, W>(top, E, F, wbuf, wfr, cnt, lane, f, j, ring, S);
             R = S;
         } else {
             if (lane == 0) ring[0] = make_uint2(0u, range_argmin<VARIANT>(0u, n_lights, E.r, E.c));
@@ -534,10 +548,10 @@ cull_single_kernel(const Launch Lc, const Frame fr) {
     traverse<VARIANT, false, W, RING, THREADS, TOP>(Lc, &fr);
 }
 
-template <int VARIANT, int W, int RING, int THREADS>
+template <int VARIANT, int W, int RING, int THREADS, int TOP>
 __global__ void __launch_bounds__(THREADS, min_blocks<W>(THREADS))
 cull_batch_kernel(const __grid_constant__ Launch Lc, const __grid_constant__ FrameArray<kMaxFrames> FA) {
-    traverse<VARIANT, true, W, RING, THREADS, 0>(Lc, FA.f);
+    traverse<VARIANT, true, W, RING, THREADS, TOP>(Lc, FA.f);
 }
 
 }  // namespace
