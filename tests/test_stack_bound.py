@@ -53,11 +53,29 @@ def _depths(t):
     return d
 
 
-def simulate(t, width, keep, lanes=32):
+def _head_frontier(t, keep, levels=6):
+    """The stack a binary walk with the head starts from: the nodes of depth levels - 1
+    that survive, in heap (left to right) order, with the visits the head accounts for (the
+    root and the surviving nodes above that depth). A node below the root survives iff
+    keep(node) holds for it and every ancestor below the root, as for the walk itself."""
+    front, visits = [0], 1
+    for depth in range(1, levels):
+        nxt = [c for g in front for c in _children(t, g) if keep(c)]
+        if depth < levels - 1:
+            visits += len(nxt)
+        front = nxt
+    return front, visits
+
+
+def simulate(t, width, keep, lanes=32, head=False):
     """Largest stack size of the chunked traversal; keep(node) decides whether a pushed
-    candidate survives its cull test. Returns (max size, visits)."""
+    candidate survives its cull test. With head (binary only), the walk starts from the
+    head's frontier at depth 5. Returns (max size, visits)."""
     stack = [0]
     peak, visits = 1, 0
+    if head:
+        stack, visits = _head_frontier(t, keep)
+        peak = len(stack)
     while stack:
         m = min(lanes, len(stack))
         popped = stack[len(stack) - m:]
@@ -98,6 +116,20 @@ def _trees():
     out.append(("chain-cost", oracle.Tree(chain, (F(2.0) ** (-np.arange(2000) % 60)).astype(F),
                                           topology="cost")))
     return out
+
+
+def test_stack_bound_holds_from_the_head():
+    # the head (binary records) starts the walk from at most 32 nodes of depth 5, one run
+    # of the proof's kind; the bound and the visit count are those of the walk from the root
+    for name, t in _trees():
+        b = bound(int(t.height), 2)
+        for p in (1.0, 0.5, 0.8, 0.95):
+            seed = int(p * 1000) + 7
+            h = lambda c, seed=seed: ((c * 0x9E3779B1 + seed * 0x85EBCA6B) & 0xFFFFFFFF) / 2.0 ** 32
+            keep = (lambda c: True) if p == 1.0 else (lambda c, h=h, p=p: h(c) < p)
+            peak, v = simulate(t, 2, keep, head=True)
+            assert peak <= b, (name, p, peak, b)
+            assert v == simulate(t, 2, keep)[1], (name, p)
 
 
 @pytest.mark.parametrize("width", [2, 4])
