@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) scene_links_kernel(const hrr_node *_
 // correctly rounded reciprocal of det.
 __device__ __forceinline__ bool segment_hits(const float e[3], const float D[3], const float *__restrict__ tri) {
     float v0x, v0y, v0z, e1x, e1y, e1z, e2x, e2y;
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(v0x), "=f"(v0y), "=f"(v0z), "=f"(e1x), "=f"(e1y), "=f"(e1z), "=f"(e2x), "=f"(e2y)
         : "l"(tri));
     const float e2z = __ldg(tri + 8);
@@ -168,11 +168,13 @@ __device__ __forceinline__ bool box_hit(const float e[3], const float inv[3], co
     return tn * (1.0f - 9.5367431640625e-07f) <= tf * (1.0f + 9.5367431640625e-07f);
 }
 
+// One 64-byte record as two 256-bit read-only loads that do not allocate in L1 (scattered
+// records are rarely reused from L1; filling it would cost L1 data-pipe cycles).
 __device__ __forceinline__ void load_record(const float4 *p, float4 &q0, float4 &q1, float4 &q2, float4 &q3) {
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(q0.x), "=f"(q0.y), "=f"(q0.z), "=f"(q0.w), "=f"(q1.x), "=f"(q1.y), "=f"(q1.z), "=f"(q1.w)
         : "l"(p));
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
         : "=f"(q2.x), "=f"(q2.y), "=f"(q2.z), "=f"(q2.w), "=f"(q3.x), "=f"(q3.y), "=f"(q3.z), "=f"(q3.w)
         : "l"(p));
 }

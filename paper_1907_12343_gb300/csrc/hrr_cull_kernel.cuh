@@ -31,9 +31,10 @@
 // spill area is sized by that bound.
 //
 // Memory: the kernel is bound by the L1 data pipe (one scattered record per lane per
-// step), so each record is fetched with 256-bit loads. A node's range minimum is attained at
-// its argmin, which lies in exactly one child; carrying the argmin with each stack entry
-// means only the other children's minima have to be computed. Accepted pairs are staged
+// step), so each record is fetched with 256-bit loads that do not allocate in L1. A node's
+// range minimum is attained at its argmin, which lies in exactly one child; carrying the
+// argmin with each stack entry means only the other children's minima have to be
+// computed. Accepted pairs are staged
 // per warp in shared memory and appended to the output with one atomic per frame and
 // coalesced 8-byte stores.
 //
@@ -104,9 +105,11 @@ __device__ __forceinline__ const Frame &frame_at(const Frame *F, uint32_t f) {
     else return F[f];
 }
 
-// 32 bytes (two float4) as one 256-bit read-only load.
+// 32 bytes (two float4) as one 256-bit read-only load that does not allocate in L1: the
+// records are scattered and rarely reused from L1, and filling it with them would take
+// L1 data-pipe cycles the kernel is bound by (they come from L2 either way).
 __device__ __forceinline__ void load32(const float4 *p, float4 &a, float4 &b) {
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
         : "l"(p));
 }

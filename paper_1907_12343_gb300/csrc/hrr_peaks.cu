@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(kPeakThreads) l2_stream_kernel(const uint4 *__
 }
 
 // Each lane fetches iters 64-byte records at pseudo-random indices of an L2-resident array
-// of n_rec records (a power of two), as two 256-bit read-only loads, the traversal's form.
+// of n_rec records (a power of two), as two 256-bit read-only loads that do not allocate
+// in L1, the traversal's form.
 __global__ void __launch_bounds__(kPeakThreads) record_fetch_kernel(const float4 *__restrict__ rec, uint32_t n_rec,
                                                                     int iters, uint32_t seed, float *sink) {
     uint32_t x = seed ^ ((blockIdx.x * kPeakThreads + threadIdx.x) * 0x9E3779B9u);
@@ -36,10 +37,10 @@ __global__ void __launch_bounds__(kPeakThreads) record_fetch_kernel(const float4
         x = x * 1664525u + 1013904223u;  // LCG step
         const float4 *p = rec + 4 * (size_t)((x >> 7) & (n_rec - 1));
         float a0, a1, a2, a3, a4, a5, a6, a7, b0, b1, b2, b3, b4, b5, b6, b7;
-        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                      : "=f"(a0), "=f"(a1), "=f"(a2), "=f"(a3), "=f"(a4), "=f"(a5), "=f"(a6), "=f"(a7)
                      : "l"(p));
-        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
+        asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
                      : "=f"(b0), "=f"(b1), "=f"(b2), "=f"(b3), "=f"(b4), "=f"(b5), "=f"(b6), "=f"(b7)
                      : "l"(p));
         acc += (((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7))) + (((b0 + b1) + (b2 + b3)) + ((b4 + b5) + (b6 + b7)));

@@ -53,11 +53,13 @@ struct SampleLaunch {
     uint2 *spill;
 };
 
+// One 64-byte record as two 256-bit read-only loads that do not allocate in L1 (scattered
+// records are rarely reused from L1; filling it would cost L1 data-pipe cycles).
 __device__ __forceinline__ void load_record(const float4 *p, float4 &q0, float4 &q1, float4 &q2, float4 &q3) {
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
         : "=f"(q0.x), "=f"(q0.y), "=f"(q0.z), "=f"(q0.w), "=f"(q1.x), "=f"(q1.y), "=f"(q1.z), "=f"(q1.w)
         : "l"(p));
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8+32];"
         : "=f"(q2.x), "=f"(q2.y), "=f"(q2.z), "=f"(q2.w), "=f"(q3.x), "=f"(q3.y), "=f"(q3.z), "=f"(q3.w)
         : "l"(p));
 }
