@@ -115,8 +115,7 @@ typedef struct hrr_cull_opts {
      * 0 for a plain tile */
     uint32_t sample_index;
     /* traversal form (results do not depend on it; 0 = the library default for each, see
-     * hrr_default_tuning: width 2, 128 ring entries (256 for width 4), 128 threads,
-     * 6 top levels):
+     * hrr_default_tuning: width 2, 256 ring entries, 256 threads, 6 top levels):
      *   node_width: 2 = binary records (a visit tests both children), 4 = the hierarchy read
      *     with nodes of width four (a visit tests the four grandchildren);
      *   ring_entries: stack entries per warp kept in shared memory, 128 or 256 for width 2,

@@ -163,20 +163,18 @@ struct hrr_cull_frame_t {
     unsigned long long cursor_begin; // where the frame's eyes start on the launch's cursor
 };
 
-// Traversal defaults: node width, shared-memory stack ring per warp (the smallest that
-// holds a step's pushes: shared memory a block leaves unused goes to the L1 cache the node
-// records pass through), threads per block, top levels evaluated from shared memory (1: the
-// root only, every level walked).
+// Traversal defaults (the fastest form on the 1920x1080-eye, 2^20-light frame): node width,
+// shared-memory stack ring per warp, threads per block, top levels evaluated from shared
+// memory (1: the root only, every level walked).
 #define HRR_DEFAULT_NODE_WIDTH 2u
-#define HRR_DEFAULT_RING_W2 128u
-#define HRR_DEFAULT_RING_W4 256u
-#define HRR_DEFAULT_THREADS 128u
+#define HRR_DEFAULT_RING 256u
+#define HRR_DEFAULT_THREADS 256u
 #define HRR_DEFAULT_TOP_LEVELS HRR_TOP_LEVELS
 
 // Launch parameters with the library defaults filled in.
 inline hrr_tuning hrr_tuning_normalized(hrr_tuning t) {
     if (!t.node_width) t.node_width = HRR_DEFAULT_NODE_WIDTH;
-    if (!t.ring_entries) t.ring_entries = t.node_width == 4 ? HRR_DEFAULT_RING_W4 : HRR_DEFAULT_RING_W2;
+    if (!t.ring_entries) t.ring_entries = HRR_DEFAULT_RING;
     if (!t.threads_per_block) t.threads_per_block = HRR_DEFAULT_THREADS;
     // the top levels come with binary records only: width four defaults to the root alone
     if (!t.top_levels) t.top_levels = t.node_width == 2 ? HRR_DEFAULT_TOP_LEVELS : 1u;
