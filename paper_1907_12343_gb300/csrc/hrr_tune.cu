@@ -2,9 +2,10 @@
 //
 // The traversal's results do not depend on its tuning (range-minimum variant, node width,
 // shared-memory stack ring, threads per block, top levels evaluated from shared memory,
-// resident blocks per SM); only its speed does. hrr_autotune_all times every compiled form, at the most resident blocks per SM that
-// fit and at one block fewer, on a caller-given eye sample; hrr_autotune keeps the fastest.
-// A caller (the Python autotuner) caches one answer per size class of workload.
+// resident blocks per SM); only its speed does. hrr_autotune_all times every compiled
+// form, at the most resident blocks per SM that fit and at one block fewer, on a
+// caller-given eye sample; hrr_autotune keeps the fastest. A caller (the Python autotuner)
+// caches one answer per size class of workload.
 #include <algorithm>
 #include <vector>
 
