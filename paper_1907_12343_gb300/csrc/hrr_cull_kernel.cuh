@@ -244,9 +244,9 @@ __device__ __forceinline__ void visit(const float4 *nodes, uint32_t n_lights, ui
     if (!int0 || !int1) {  // leaf children: one test site, a second for two leaves
         const uint32_t i = !int0 ? split : last;
         const float4 ql = !int0 ? q0 : q2;
-        if (hrr_leaf_accepts(__brev(i) + E.r, E.tau, ql.x, ql.y, ql.z, ql.w, E.x, E.y, E.z)) V.acc[0] = i;
+        if (hrr_leaf_accepts(__brev(i) + E.r, E.tau, E.scale, ql.x, ql.y, ql.z, ql.w, E.x, E.y, E.z)) V.acc[0] = i;
         if (!int0 && !int1 &&
-            hrr_leaf_accepts(__brev(last) + E.r, E.tau, q2.x, q2.y, q2.z, q2.w, E.x, E.y, E.z))
+            hrr_leaf_accepts(__brev(last) + E.r, E.tau, E.scale, q2.x, q2.y, q2.z, q2.w, E.x, E.y, E.z))
             V.acc[1] = last;
     }
 }
@@ -308,7 +308,7 @@ __device__ __forceinline__ void visit(const float4 *wide, uint32_t n_lights, uin
 #pragma unroll
         for (int t = 0; t < 4; ++t)
             if (a[t] == b[t] &&
-                hrr_leaf_accepts(__brev(a[t]) + E.r, E.tau, q[2 * t].x, q[2 * t].y, q[2 * t].z, q[2 * t].w, E.x,
+                hrr_leaf_accepts(__brev(a[t]) + E.r, E.tau, E.scale, q[2 * t].x, q[2 * t].y, q[2 * t].z, q[2 * t].w, E.x,
                                  E.y, E.z))
                 V.acc[t] = a[t];
     }
@@ -351,7 +351,7 @@ __device__ __forceinline__ uint32_t head(const float4 *top, const Eye &E, const 
                 vis = survives(E, a, h, karg);
                 node = __float_as_uint(x.y);
             } else if (kind == HRR_TOP_LEAF &&
-                       hrr_leaf_accepts(__brev(first) + E.r, E.tau, a.x, a.y, a.z, a.w, E.x, E.y, E.z)) {
+                       hrr_leaf_accepts(__brev(first) + E.r, E.tau, E.scale, a.x, a.y, a.z, a.w, E.x, E.y, E.z)) {
                 acc[0] = first;
             }
         }
@@ -440,7 +440,7 @@ __device__ __forceinline__ void traverse(const Launch &Lc, const Frame *F) {
             for (int t = 0; t < W; ++t) acc[t] = kNone;
             if (lane == 0) {
                 const float4 q0 = __ldg(&nodes[0]);
-                if (hrr_leaf_accepts(__brev(0u) + E.r, E.tau, q0.x, q0.y, q0.z, q0.w, E.x, E.y, E.z)) acc[0] = 0;
+                if (hrr_leaf_accepts(__brev(0u) + E.r, E.tau, E.scale, q0.x, q0.y, q0.z, q0.w, E.x, E.y, E.z)) acc[0] = 0;
                 if (fr.eye_visits) fr.eye_visits[j] = 0;
             }
             emit<BATCH, W>(F, wbuf, wfr, cnt, lane, f, j, acc);

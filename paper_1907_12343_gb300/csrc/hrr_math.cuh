@@ -123,7 +123,14 @@ __device__ __forceinline__ uint32_t hrr_range_argmin_select(uint32_t a, uint32_t
 // Exact per-pair test (round to nearest, canonical order, no FMA): accept iff
 // xi < ceil(p 2^32), p = min(1, (tau I) / max(d2, 1e-4)). For 0 < p < 1, p 2^32 is an
 // exact float below 2^32, so its ceiling fits in 32 bits.
-__device__ __forceinline__ bool hrr_leaf_accepts(uint32_t xi, float tau, float lx, float ly,
+//
+// Most tested pairs are rejected, so the test first applies the node test to the light
+// alone (a box of one point; den is exactly the pair's max(d2, 1e-4); scale =
+// hrr_node_scale(tau)): when RD(RD(xi) den) >= RU(scale I), xi is at least the pair's
+// threshold by the node test's soundness, and the pair is rejected without the division.
+// Only the pairs that test leaves undecided go on to the exact quotient, so the result is
+// the exact rule's in every case.
+__device__ __forceinline__ bool hrr_leaf_accepts(uint32_t xi, float tau, float scale, float lx, float ly,
                                                  float lz, float inten, float ex, float ey,
                                                  float ez) {
     const float dx = __fsub_rn(lx, ex);
@@ -132,8 +139,10 @@ __device__ __forceinline__ bool hrr_leaf_accepts(uint32_t xi, float tau, float l
     float d2 = __fmul_rn(dx, dx);
     d2 = __fadd_rn(d2, __fmul_rn(dy, dy));
     d2 = __fadd_rn(d2, __fmul_rn(dz, dz));
+    const float den = fmaxf(d2, 1e-4f);
+    if (__fmul_rd(__uint2float_rd(xi), den) >= __fmul_ru(scale, inten)) return false;
     const float num = __fmul_rn(tau, inten);
-    const float p = fminf(1.0f, __fdiv_rn(num, fmaxf(d2, 1e-4f)));
+    const float p = fminf(1.0f, __fdiv_rn(num, den));
     if (p >= 1.0f) return true;
     if (!(p > 0.0f)) return false;
     return xi < __float2uint_ru(__fmul_rn(p, 4294967296.0f));

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cull_samples_kernel(cons
             uint32_t acc = 0;
             for (uint32_t s = 0; s < P.n_samples; ++s) {
                 const uint32_t rs = __shfl_sync(0xFFFFFFFFu, rl, s);
-                if (lane == 0 && hrr_leaf_accepts(__brev(0u) + rs, tau, q0.x, q0.y, q0.z, q0.w, ex, ey, ez))
+                if (lane == 0 && hrr_leaf_accepts(__brev(0u) + rs, tau, scale, q0.x, q0.y, q0.z, q0.w, ex, ey, ez))
                     acc |= 1u << s;
             }
             emit(P, wbuf, wsmp, cnt, lane, j, 0u, acc);
@@ -210,13 +210,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) cull_samples_kernel(cons
                     if (int0) {
                         const uint32_t k = hrr_range_argmin_select(first, split + 1u, cs);
                         if (!hrr_node_culls(__brev(k) + rs, den0, rhs0)) mask0 |= bit;
-                    } else if (hrr_leaf_accepts(__brev(split) + rs, tau, q0.x, q0.y, q0.z, q0.w, ex, ey, ez)) {
+                    } else if (hrr_leaf_accepts(__brev(split) + rs, tau, scale, q0.x, q0.y, q0.z, q0.w, ex, ey, ez)) {
                         acc0 |= bit;
                     }
                     if (int1) {
                         const uint32_t k = hrr_range_argmin_select(split + 1u, last + 1u, cs);
                         if (!hrr_node_culls(__brev(k) + rs, den1, rhs1)) mask1 |= bit;
-                    } else if (hrr_leaf_accepts(__brev(last) + rs, tau, q2.x, q2.y, q2.z, q2.w, ex, ey, ez)) {
+                    } else if (hrr_leaf_accepts(__brev(last) + rs, tau, scale, q2.x, q2.y, q2.z, q2.w, ex, ey, ez)) {
                         acc1 |= bit;
                     }
                 }
