@@ -179,3 +179,59 @@ def test_node_culls_zero_and_saturated():
     inside = np.array([1.5, 1.5, 1.5], F)
     f = oracle.node_cull_floor(F(0.5) * F(1e-4), lo, hi, F(1), inside)
     assert (1 << 31) <= f <= (1 << 31) + 2**10
+
+
+def _u32_to_float_rd(x: int) -> np.float32:
+    """The float32 at or below the integer x (truncation of its low bits)."""
+    h = x.bit_length()
+    if h > 24:
+        x = (x >> (h - 24)) << (h - 24)
+    return F(x)
+
+
+def _shortcut_floor(den, rhs) -> int:
+    """Smallest xi in [0, 2^32] for which RD(RD(xi) den) >= rhs (2^32: none), by bisection
+    (the left side is monotone in xi)."""
+    def rejects(xi):
+        return oracle.fround("mul", _u32_to_float_rd(xi), den, -1) >= rhs
+    if not rejects(2 ** 32 - 1):
+        return 2 ** 32
+    lo, hi = -1, 2 ** 32 - 1  # rejects(hi) holds; lo below every rejected value
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if rejects(mid):
+            hi = mid
+        else:
+            lo = mid
+    return hi
+
+
+def test_leaf_shortcut_rejects_only_rejected_pairs():
+    # The GPU leaf test first rejects a pair when RD(RD(xi) den) >= RU(s I), with den the
+    # pair's own max(d2, 1e-4) (round to nearest, canonical order: the exact rule's) and
+    # s = RU(tau 2^32 (1 + 2^-22)) (the node test's scale). Whenever it rejects, the exact
+    # rule must reject too: the smallest xi it rejects is at least ceil(p 2^32), for lights
+    # near and far, bright, dark and negative, and at the distance floor.
+    rng = np.random.default_rng(41)
+    tight = 0
+    for _ in range(3000):
+        e = rng.random(3).astype(F)
+        l = (e + rng.normal(scale=10.0 ** rng.uniform(-3, 0), size=3)).astype(F)
+        if rng.random() < 0.1:
+            l = e.copy()  # at the distance floor
+        inten = F(np.exp(rng.normal() * 2.0))
+        if rng.random() < 0.05:
+            inten = F(-inten)
+        tau = F(10.0 ** rng.uniform(-7, -1))
+        thr = oracle.leaf_threshold(tau, l, inten, e)
+        dx, dy, dz = (oracle.fround("sub", l[k], e[k], 0) for k in range(3))
+        d2 = oracle.fround("mul", dx, dx, 0)
+        d2 = oracle.fround("add", d2, oracle.fround("mul", dy, dy, 0), 0)
+        d2 = oracle.fround("add", d2, oracle.fround("mul", dz, dz, 0), 0)
+        den = max(d2, F(1e-4))
+        s = oracle.fround("mul", F(tau * F(2.0 ** 32)), F(1.0) + F(2.0 ** -22), +1)
+        floor = _shortcut_floor(den, oracle.fround("mul", s, inten, +1))
+        assert floor >= thr, (tau, l, inten, e, floor, thr)
+        if thr < 2 ** 32 and floor - thr <= max(4, thr * 2.0 ** -20):
+            tight += 1
+    assert tight > 2000  # the shortcut decides almost every rejection (within 2^-20)
