@@ -62,3 +62,14 @@ def test_null_arguments_are_rejected(lib_path):
     assert hrr.hrr_destroy(None) == hrr.HRR_ERR_INVALID_ARG
     assert hrr.hrr_launch_count(None, None) == hrr.HRR_ERR_INVALID_ARG
     assert hrr.hrr_tree_perm(None, None) == hrr.HRR_ERR_INVALID_ARG
+
+
+def test_default_tuning_is_the_documented_form(lib_path):
+    # host code only: binary records with the head over the top six levels, a 256-entry
+    # stack ring, 256-thread blocks, the branch-free range minimum, as many blocks as fit
+    import paper_1907_12343_gb300 as hrr
+    assert hrr.default_tuning() == {"rangemin_variant": 0, "blocks_per_sm": 0, "node_width": 2,
+                                    "ring_entries": 256, "threads_per_block": 256, "top_levels": 6}
+    t = hrr.hrr_tuning()
+    assert hrr.hrr_default_tuning(None) == hrr.HRR_ERR_INVALID_ARG
+    assert hrr.hrr_default_tuning(ctypes.byref(t)) == hrr.HRR_OK
