@@ -1,8 +1,8 @@
 """Per-size-class autotuning of the traversal's form and launch shape, cached in JSON.
 
 The traversal gives identical results for every tuning (range-minimum variant, node
-width, shared-memory stack ring, threads per block, resident blocks per SM); only its
-speed depends on the workload.
+width, top levels evaluated from shared memory, shared-memory stack ring, threads per
+block, resident blocks per SM); only its speed depends on the workload.
 ``Autotuner`` keys workloads by size class (bit lengths of N_l and N_e), tunes a class
 once on a sample of its eyes with ``hrr_autotune`` and stores the answer, so later
 frames, batches and servers of that class reuse it.
